@@ -1,0 +1,239 @@
+// Internal declarations of libskel.so shared by the host runtime (api.cpp)
+// and the kernel translation units (k_*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "skel.h"
+
+namespace skel {
+
+// ----------------------------------------------------------------- errors --
+// Sets the thread-local message returned by skel_last_error and returns code.
+int fail(int code, const std::string &msg);
+int fail_cuda(cudaError_t e, const char *what);
+
+#define SKEL_CUDA_TRY(expr)                                   \
+    do {                                                      \
+        cudaError_t e_ = (expr);                              \
+        if (e_ != cudaSuccess) return ::skel::fail_cuda(e_, #expr); \
+    } while (0)
+
+// ---------------------------------------------------------------- device --
+struct DeviceInfo {
+    int device;
+    int sms;                  // multiprocessor count (152 on GB300)
+    int max_smem_optin;       // bytes of shared memory a block may opt into
+    size_t l2_bytes;
+};
+const DeviceInfo &device_info();  // of the current device
+
+// ------------------------------------------------------- scratch memory --
+// Layout of a scratch block: a 256-byte control block, a region of look-back
+// flag words, then the data region.  Kernels leave the control counters at
+// zero when they finish.  The flag region holds nothing but flag words
+// (epoch << 2 | status), so a stale word can only carry an older epoch.
+struct Control {
+    uint32_t ticket;     // tile ticket counter (single-pass scan, batched)
+    uint32_t done;       // blocks finished (single-pass reduce)
+    uint32_t error;      // device-side status bits (kErrTimeout)
+    uint32_t abort;      // epoch of a call whose bounded wait gave up; its other waiters stop
+    uint32_t queue;      // work queue of persistent kernels
+    uint32_t exited;     // persistent blocks that left the work loop
+    uint32_t pad[58];
+};
+static_assert(sizeof(Control) == 256, "control block is 256 bytes");
+constexpr uint32_t kErrTimeout = 1u;   // a bounded wait gave up
+constexpr uint32_t kErrInput = 2u;     // device-resident input failed validation (batched offsets)
+
+struct Scratch {
+    Control *ctl;        // device address of the control block
+    uint32_t *flags;     // look-back flag words (flag_count requested)
+    unsigned char *data; // device address of the data region (256-byte aligned)
+    size_t data_bytes;
+    uint32_t epoch;      // tag of this call's look-back flags (never 0)
+};
+
+// Returns scratch for `stream` with at least `data_bytes` of data region and
+// `flag_count` flag words.  Scratch is cached per (device, stream) and reused
+// by later calls on the same stream (stream order serialises them).  A call
+// asking for flags gets a fresh epoch (the flags are cleared when the epoch
+// counter wraps or the flag region grows).
+int get_scratch(cudaStream_t stream, size_t data_bytes, size_t flag_count, Scratch *out);
+
+// Control block of the scratch of `stream`, or nullptr if none was made.
+Control *scratch_control(cudaStream_t stream);
+int release_scratch();
+// Fixed 256-byte device buffer of `stream` for scalar results.
+int result_slot(cudaStream_t stream, void **out);
+
+// Allocation through the active allocator; free_dev must be given the same
+// allocator record that allocated.
+struct Allocator {
+    void *(*alloc)(size_t, void *, void *);
+    void (*free_fn)(void *, void *, void *);
+    void *ctx;
+};
+Allocator current_allocator();
+void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t stream);
+void dev_free(const Allocator &a, void *p, cudaStream_t stream);
+
+// ------------------------------------------------------------- debugging --
+struct DebugKnobs {
+    int64_t scan_skip_publish_tile;  // -1: off
+    uint64_t wait_limit_ns;          // bounded-wait limit
+};
+DebugKnobs debug_knobs();
+int set_debug(int key, int64_t value);
+
+// --------------------------------------------------------------- dispatch --
+struct Choice {
+    int variant;
+    int block;
+    int ept;
+    int tile;
+};
+
+// Context of a call (the key of the execution-plan table).
+struct Context {
+    int skeleton;
+    int fn;
+    int dtype;
+    int64_t n;
+    int radius;
+    int residency;  // 0: operands device-valid; 1: at least one needs a host->device copy
+};
+
+int bucket_of(int64_t n);
+// Table lookup with nearest-bucket extrapolation; falls back to the
+// skeleton's built-in default.  Honors skel_force_variant.  *forced is set
+// when the choice came from a force.
+Choice select_variant(const Context &ctx, bool *forced);
+void record_last(int skeleton, const Choice &c);
+int last_choice(int skeleton, Choice *c);
+int force_variant(int skeleton, const Choice &c);
+int dispatch_set(int sk, int fn, int dt, int bucket, int radius, int res, const Choice &c);
+int dispatch_size();
+int dispatch_load(const char *path);
+Choice skeleton_default(int skeleton);
+void set_allocator(const Allocator &a);
+const char *last_error_cstr();
+void clear_error();
+
+// ------------------------------------------------------ kernel launchers --
+// Each launcher validates its own selectability constraint: it returns
+// SKEL_ERR_UNSUPPORTED (with a message) when the chosen variant cannot run
+// this call, so that the caller can fall back to the default variant.
+
+struct MapLaunch {
+    int fn;
+    float a;
+    const float *in0;
+    const float *in1;
+    float *out;
+    int64_t n;
+};
+int launch_map(const MapLaunch &m, const Choice &c, cudaStream_t s);
+int map_variant_count();
+const char *map_variant_name(int v);
+Choice map_default();
+
+struct ReduceLaunch {
+    int op;         // SKEL_FN_ADD / SKEL_FN_MAX
+    int map_fn;     // -1 (plain reduce), SKEL_FN_MUL, SKEL_FN_SQ
+    int dtype;      // SKEL_F32 / SKEL_I32
+    const void *in0;
+    const void *in1;
+    void *out;      // device address of the 1-element result
+    int64_t n;
+};
+int launch_reduce(const ReduceLaunch &r, const Choice &c, cudaStream_t s);
+int reduce_variant_count();
+const char *reduce_variant_name(int v);
+Choice reduce_default();
+
+struct ScanLaunch {
+    int dtype;      // SKEL_F32 / SKEL_I32
+    bool inclusive;
+    bool reverse;   // scan from the end (the adjoint of scan)
+    const void *in;
+    void *out;
+    int64_t n;      // total elements
+    int64_t seg;    // segment length for row-wise scans (0: one segment)
+};
+int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s);
+int scan_variant_count();
+const char *scan_variant_name(int v);
+Choice scan_default();
+
+struct StencilLaunch {
+    int ndim;            // 1 or 2
+    int radius;
+    int boundary;
+    const float *w;      // host copy of weights: 2r+1 (1D) or 9 (2D, row-major 3x3)
+    int taps5;           // 2D: 1 if the 5-point cross (corner weights ignored)
+    const float *in;
+    float *out;
+    int64_t rows, cols;  // 1D: rows = 1, cols = n
+    bool transpose;      // adjoint (mirrored weights, clamp folding)
+};
+int launch_stencil(const StencilLaunch &st, const Choice &c, cudaStream_t s);
+int stencil_variant_count(int ndim);
+const char *stencil_variant_name(int ndim, int v);
+Choice stencil_default(int ndim);
+
+struct MapArrayLaunch {
+    int fn;              // SKEL_FN_GATHER / SKEL_FN_ROWDOT
+    const float *A;
+    int64_t m;
+    const void *B;       // int32 indices (gather) or float rows n x m (rowdot)
+    float *out;
+    int64_t n;
+};
+int launch_maparray(const MapArrayLaunch &ma, const Choice &c, cudaStream_t s);
+int maparray_variant_count();
+const char *maparray_variant_name(int v);
+Choice maparray_default();
+
+struct BatchedLaunch {
+    bool want_reduce;
+    bool want_scan;
+    bool inclusive;
+    const float *values;
+    const int64_t *offsets;   // B+1 entries (device)
+    int64_t B;
+    int64_t total;            // offsets[B] (host-known length of values)
+    float *results;           // B (may be NULL)
+    float *scan_out;          // total (may be NULL)
+};
+// Scratch the batched launch needs for this call: data bytes and look-back
+// flag words (upper bounds from the total length and the instance count; the
+// plan allocates them itself, the direct call uses the stream's scratch).
+size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c);
+size_t batched_flag_count(const BatchedLaunch &b, const Choice &c);
+int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags,
+                   unsigned char *data, uint32_t epoch, cudaStream_t s);
+int batched_variant_count();
+const char *batched_variant_name(int v);
+Choice batched_default();
+
+// Backward helpers (elementwise adjoints and broadcasts).
+struct MapBwdLaunch {
+    int fn;
+    float a;
+    int tanh_from_output;
+    const float *in0;
+    const float *in1;
+    const float *g;      // per-element upstream gradient (NULL: use *g_scalar)
+    const float *g_scalar_dev;  // device scalar (mapreduce/reduce adjoint), or NULL
+    float g_scalar_host;
+    float *gin0;
+    float *gin1;
+    int64_t n;
+};
+int launch_map_bwd(const MapBwdLaunch &m, cudaStream_t s);
+
+}  // namespace skel

@@ -1,0 +1,184 @@
+// MapArray skeleton: out[i] = f(A, B[i]) with A read whole (random access)
+// and B per element.  The paper names no MapArray; the reading implemented:
+//   GATHER  out[i] = A[clamp(idx[i], 0, m-1)]          (idx int32)
+//   ROWDOT  out[i] = sum_k A[k] * M[i, k]               (M row-major n x m)
+// Variants (gather / rowdot):
+//   0 scalar      gather: one output per thread; rowdot: one row per thread
+//                 (no constraints; the baseline).
+//   1 vec4        gather: 16-byte index loads and output stores, four outputs
+//                 per thread; rowdot: one warp per row, 16-byte coalesced
+//                 row loads, warp-shuffle sum.
+//   2 block_row   rowdot only: one block per row, block-tree sum (long rows).
+// A is read through the read-only path; it stays in L1/L2 across rows.
+#include "common.cuh"
+
+namespace skel {
+namespace {
+
+__device__ __forceinline__ int64_t clampi(int64_t k, int64_t m) { return k < 0 ? 0 : (k >= m ? m - 1 : k); }
+
+__global__ void gather_scalar(const float *__restrict__ A, int64_t m, const int32_t *__restrict__ idx,
+                              float *__restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __ldg(A + clampi(idx[i], m));
+}
+
+__global__ void gather_vec4(const float *__restrict__ A, int64_t m, const int32_t *__restrict__ idx,
+                            float *__restrict__ out, int64_t n)
+{
+    const int64_t nv = n / 4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 k = dev::ld_stream(reinterpret_cast<const uint4 *>(idx) + i);
+        float4 o;
+        o.x = __ldg(A + clampi((int32_t)k.x, m));
+        o.y = __ldg(A + clampi((int32_t)k.y, m));
+        o.z = __ldg(A + clampi((int32_t)k.z, m));
+        o.w = __ldg(A + clampi((int32_t)k.w, m));
+        dev::st_stream(reinterpret_cast<float4 *>(out) + i, o);
+    }
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n - 4 * nv) out[4 * nv + t] = __ldg(A + clampi(idx[4 * nv + t], m));
+}
+
+__global__ void rowdot_thread(const float *__restrict__ A, int64_t m, const float *__restrict__ M,
+                              float *__restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float *row = M + i * m;
+        float acc = 0.f;
+        for (int64_t k = 0; k < m; ++k) acc = fmaf(__ldg(A + k), row[k], acc);
+        out[i] = acc;
+    }
+}
+
+// One warp per row; VEC: row start and A 16-byte aligned, m % 4 == 0.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+rowdot_warp(const float *__restrict__ A, int64_t m, const float *__restrict__ M, float *__restrict__ out, int64_t n)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); i < n; i += warps) {
+        const float *row = M + i * m;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (VEC) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+            const float4 *A4 = reinterpret_cast<const float4 *>(A);
+            const int64_t mv = m / 4;
+            int64_t k = lane;
+            for (; k + 32 < mv; k += 64) {   // two 16-byte loads in flight per lane
+                const float4 p = dev::ld_stream(r4 + k), q = dev::ld_stream(r4 + k + 32);
+                const float4 ap = __ldg(A4 + k), aq = __ldg(A4 + k + 32);
+                a0 = fmaf(ap.x, p.x, a0); a1 = fmaf(ap.y, p.y, a1); a2 = fmaf(ap.z, p.z, a2); a3 = fmaf(ap.w, p.w, a3);
+                a0 = fmaf(aq.x, q.x, a0); a1 = fmaf(aq.y, q.y, a1); a2 = fmaf(aq.z, q.z, a2); a3 = fmaf(aq.w, q.w, a3);
+            }
+            for (; k < mv; k += 32) {
+                const float4 p = dev::ld_stream(r4 + k);
+                const float4 ap = __ldg(A4 + k);
+                a0 = fmaf(ap.x, p.x, a0); a1 = fmaf(ap.y, p.y, a1); a2 = fmaf(ap.z, p.z, a2); a3 = fmaf(ap.w, p.w, a3);
+            }
+        } else {
+            for (int64_t k = lane; k < m; k += 32) a0 = fmaf(__ldg(A + k), row[k], a0);
+        }
+        float acc = (a0 + a1) + (a2 + a3);
+        acc = dev::warp_reduce<dev::AddF>(acc);
+        if (lane == 0) out[i] = acc;
+    }
+}
+
+// One block per row (grid-stride over rows); VEC as above.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+rowdot_block(const float *__restrict__ A, int64_t m, const float *__restrict__ M, float *__restrict__ out, int64_t n)
+{
+    __shared__ float smem[32];
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const float *row = M + i * m;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (VEC) {
+            const float4 *r4 = reinterpret_cast<const float4 *>(row);
+            const float4 *A4 = reinterpret_cast<const float4 *>(A);
+            for (int64_t k = threadIdx.x; k < m / 4; k += 256) {
+                const float4 p = dev::ld_stream(r4 + k);
+                const float4 ap = __ldg(A4 + k);
+                a0 = fmaf(ap.x, p.x, a0); a1 = fmaf(ap.y, p.y, a1); a2 = fmaf(ap.z, p.z, a2); a3 = fmaf(ap.w, p.w, a3);
+            }
+        } else {
+            for (int64_t k = threadIdx.x; k < m; k += 256) a0 = fmaf(__ldg(A + k), row[k], a0);
+        }
+        const float acc = dev::block_reduce<dev::AddF, float, 256>((a0 + a1) + (a2 + a3), smem);
+        if (threadIdx.x == 0) out[i] = acc;
+    }
+}
+
+int check_launch(const char *what)
+{
+    cudaError_t e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), what);
+}
+
+unsigned grid_for(int64_t work, int block)
+{
+    int64_t g = ceil_div(work, block);
+    const int64_t cap = (int64_t)device_info().sms * (2048 / block) * 8;
+    if (g > cap) g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+int maparray_variant_count() { return 3; }
+const char *maparray_variant_name(int v)
+{
+    static const char *names[] = {"scalar", "vec4", "block_row"};
+    return v >= 0 && v < 3 ? names[v] : "?";
+}
+Choice maparray_default() { return Choice{1, 256, 0, 0}; }
+
+int launch_maparray(const MapArrayLaunch &ma, const Choice &c, cudaStream_t s)
+{
+    if (ma.n == 0) return SKEL_OK;
+    const int block = 256;
+    if (c.block > 0 && c.block != block) return fail(SKEL_ERR_INVALID_ARG, "maparray: block must be 256");
+    if (ma.fn == SKEL_FN_GATHER) {
+        const int32_t *idx = static_cast<const int32_t *>(ma.B);
+        if (c.variant == 0) {
+            gather_scalar<<<grid_for(ma.n, block), block, 0, s>>>(ma.A, ma.m, idx, ma.out, ma.n);
+            return check_launch("gather scalar");
+        }
+        if (c.variant == 1) {
+            if (!aligned16(idx) || !aligned16(ma.out))
+                return fail(SKEL_ERR_UNSUPPORTED, "gather vec4: 16-byte aligned operands needed");
+            gather_vec4<<<grid_for(ceil_div(ma.n, 4), block), block, 0, s>>>(ma.A, ma.m, idx, ma.out, ma.n);
+            return check_launch("gather vec4");
+        }
+        return fail(SKEL_ERR_UNSUPPORTED, "gather: variant not offered");
+    }
+    if (ma.fn == SKEL_FN_ROWDOT) {
+        const float *M = static_cast<const float *>(ma.B);
+        const bool vec = aligned16(M) && aligned16(ma.A) && ma.m % 4 == 0;
+        if (c.variant == 0) {
+            rowdot_thread<<<grid_for(ma.n, block), block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            return check_launch("rowdot thread");
+        }
+        if (c.variant == 1) {
+            const unsigned g = grid_for(ceil_div(ma.n, 8) * 256, block);
+            if (vec) rowdot_warp<true><<<g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            else rowdot_warp<false><<<g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            return check_launch("rowdot warp");
+        }
+        if (c.variant == 2) {
+            int64_t g = ma.n;
+            const int64_t cap = (int64_t)device_info().sms * 8 * 16;
+            if (g > cap) g = cap;
+            if (vec) rowdot_block<true><<<(unsigned)g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            else rowdot_block<false><<<(unsigned)g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            return check_launch("rowdot block");
+        }
+        return fail(SKEL_ERR_INVALID_ARG, "rowdot: unknown variant");
+    }
+    return fail(SKEL_ERR_UNSUPPORTED, "maparray: fn must be GATHER or ROWDOT");
+}
+
+}  // namespace skel

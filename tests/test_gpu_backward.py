@@ -1,0 +1,142 @@
+"""Parity of the hand-written backward kernels (Map, Reduce, MapReduce,
+Scan; MapOverlap's adjoint is in test_gpu_mapoverlap.py) and of the
+differentiable composed pipeline behind torch.autograd.Function, against the
+oracle gradient and central finite differences."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from helpers import (SUM_REL, assert_elem_close, assert_prefix_close, dev_empty, dev_tensor, skel, to_np,
+                     wrap)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("fn", ["axpy", "add", "sub", "mul", "tanh", "sq", "scale", "copy"])
+@pytest.mark.parametrize("n,pad", [(1, 0), (5, 0), (100_003, 0), (100_003, 1)])
+def test_map_bwd(fn, n, pad):
+    import torch
+    sk = skel()
+    two = fn in ("axpy", "add", "sub", "mul")
+    x, y, g = syn.uniform_f32(1, n), syn.uniform_f32(2, n), syn.uniform_f32(3, n)
+    ins = [wrap(dev_tensor(x, pad))] + ([wrap(dev_tensor(y, pad))] if two else [])
+    gx = dev_empty((n,), torch.float32, pad)
+    gy = dev_empty((n,), torch.float32, pad) if two else None
+    sk.skel_map_bwd(fn, ins, wrap(dev_tensor(g, pad)), [wrap(gx)] + ([wrap(gy)] if two else []),
+                    params=[2.5] if fn in ("axpy", "scale") else [])
+    rx, ry = oracle.map_bwd_f32(fn if fn != "copy" else "copy", g, x, y if two else None, a=2.5)
+    assert_elem_close(to_np(gx), rx, f"{fn} dx")
+    if two:
+        assert_elem_close(to_np(gy), ry, f"{fn} dy")
+
+
+def test_tanh_bwd_from_saved_output():
+    import torch
+    sk = skel()
+    n = 50_001
+    x, g = syn.uniform_f32(4, n, -3, 3), syn.uniform_f32(5, n)
+    t = torch.tanh(dev_tensor(x)) * 0   # placeholder buffer, filled by the skeleton below
+    sk.skel_map("tanh", [wrap(dev_tensor(x))], wrap(t))
+    gx = dev_empty((n,), torch.float32)
+    sk.skel_map_bwd("tanh", [wrap(t)], wrap(dev_tensor(g)), [wrap(gx)], params=[1.0])
+    rx, _ = oracle.map_bwd_f32("tanh", g, x)
+    assert_elem_close(to_np(gx), rx, "tanh from output", atol=2e-6)
+
+
+@pytest.mark.parametrize("n", [1, 4097, 1_000_003])
+def test_reduce_and_mapreduce_bwd(n):
+    import torch
+    sk = skel()
+    x, y = syn.uniform_f32(6, n), syn.uniform_f32(7, n)
+    gr = torch.tensor([0.375], device="cuda")
+    gx = dev_empty((n,), torch.float32)
+    sk.skel_reduce_bwd("add", wrap(gr), wrap(gx))
+    assert np.all(to_np(gx) == np.float32(0.375))
+    sk.skel_reduce_bwd("add", None, wrap(gx), gr_host=-2.0)
+    assert np.all(to_np(gx) == -2.0)
+    gy = dev_empty((n,), torch.float32)
+    sk.skel_mapreduce_bwd("mul", "add", [wrap(dev_tensor(x)), wrap(dev_tensor(y))], wrap(gr), [wrap(gx), wrap(gy)])
+    assert_elem_close(to_np(gx), 0.375 * y.astype(np.float64), "dot dx")
+    assert_elem_close(to_np(gy), 0.375 * x.astype(np.float64), "dot dy")
+    sk.skel_mapreduce_bwd("sq", "add", [wrap(dev_tensor(x))], wrap(gr), [wrap(gx)])
+    assert_elem_close(to_np(gx), oracle.map_bwd_f32("sq", np.full(n, 0.375, np.float32), x)[0], "sumsq dx")
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("n", [1, 3, 4095, 4097, 1_000_003, 1 << 22])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_bwd(variant, n, inclusive):
+    import torch
+    from helpers import forced
+    sk = skel()
+    g = syn.uniform_f32(8, n)
+    out = dev_empty((n,), torch.float32)
+    with forced("scan", variant):
+        sk.skel_scan_bwd("add", inclusive, wrap(dev_tensor(g)), wrap(out))
+    ref, ab = oracle.scan_bwd_f32(g, inclusive)
+    assert_prefix_close(to_np(out), ref, ab, f"reverse scan n={n}")
+
+
+@pytest.mark.parametrize("rows,cols", [(3, 4096), (5, 1001), (2, 8192)])
+def test_scan_bwd_rows(rows, cols):
+    import torch
+    sk = skel()
+    g = syn.uniform_f32(9, rows * cols).reshape(rows, cols)
+    out = dev_empty((rows, cols), torch.float32)
+    sk.skel_scan_bwd("add", True, wrap(dev_tensor(g)), wrap(out))
+    o = to_np(out)
+    for r in range(rows):
+        ref, ab = oracle.scan_bwd_f32(g[r], True)
+        assert_prefix_close(o[r], ref, ab, f"row {r}")
+
+
+def grad_tolerance(x, g_ref):
+    """Per-element bound of the composed gradient: 1e-6 * max(1, |g|) for the
+    elementwise and stencil paths, plus 2^-20 times the absolute reverse-scan
+    sums of the scan path (its float32 rounding)."""
+    rows, cols = x.shape
+    t = np.tanh(x.astype(np.float64))
+    s_abs = np.cumsum(np.abs(t), axis=1)                  # |prefix| bound of the forward row scan
+    gs_abs = 2.0 * s_abs / x.size                         # |upstream| of the reverse scan
+    suffix = np.cumsum(gs_abs[:, ::-1], axis=1)[:, ::-1]
+    return 1e-6 * np.maximum(1.0, np.abs(g_ref)) + 2 * SUM_REL * suffix
+
+
+@pytest.mark.parametrize("shape", [(16, 16), (64, 100), (257, 300)])
+def test_composed_loss_small(shape):
+    import torch
+    from paper_1405_2915_gb300.autograd import composed_loss
+    x = syn.uniform_f32(syn.SEED_GRAD, shape[0] * shape[1]).reshape(shape)
+    xt = dev_tensor(x).requires_grad_(True)
+    L = composed_loss(xt)
+    L.backward()
+    Lr, gr = oracle.composed_loss_f32(x, 1, oracle.stencil_weights("9pt"), "clamp")
+    assert abs(float(L.item()) - Lr) <= SUM_REL * abs(Lr) * 4
+    g = to_np(xt.grad)
+    assert np.all(np.abs(g - gr) <= grad_tolerance(x, gr))
+
+
+def test_composed_loss_8192_fd_and_oracle_gradient():
+    """The differentiable workload: 8192 x 8192 grid, U[-1,1]; GPU gradient vs
+    the float64 oracle gradient at every point, and vs central finite
+    differences (h = 1e-3) of the float64 oracle at 64 seeded probes."""
+    import torch
+    from paper_1405_2915_gb300.autograd import composed_loss
+    W = 8192
+    x = syn.uniform_f32(syn.SEED_GRAD, W * W).reshape(W, W)
+    xt = dev_tensor(x).requires_grad_(True)
+    L = composed_loss(xt)
+    L.backward()
+    g = to_np(xt.grad)
+    w9 = oracle.stencil_weights("9pt")
+    Lr, gr = oracle.composed_loss_f32(x, 1, w9, "clamp")
+    assert abs(float(L.item()) - Lr) <= SUM_REL * abs(Lr) * 4
+    assert np.all(np.abs(g - gr) <= grad_tolerance(x, gr))
+    probes = syn.splitmix64(syn.SEED_GRAD + 1, 64) % np.uint64(W * W)
+    h = 1e-3
+    for p in probes:
+        i, j = divmod(int(p), W)
+        fd = (oracle.composed_loss_delta_f32(x, 1, w9, i, j, h) -
+              oracle.composed_loss_delta_f32(x, 1, w9, i, j, -h)) / (2 * h)
+        assert abs(g[i, j] - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, g[i, j], fd)

@@ -1,0 +1,97 @@
+"""Parity of Scan (every variant, forced): int32 bit-exact modulo 2^32;
+float32 per element within 2^-20 * sum_{j<=i} |x_j| (the prefix of |x| over
+the same index range)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from helpers import assert_prefix_close, dev_empty, dev_tensor, forced, skel, to_np, wrap
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
+SCAN_CONFIGS = [(0, 4), (0, 2), (1, 4), (1, 2), (1, 8), (2, 4), (2, 8)]
+
+
+def mod32(a):
+    return np.asarray(a, dtype=np.int64).astype(np.int32)
+
+
+@pytest.mark.parametrize("variant,ept", SCAN_CONFIGS)
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("inclusive", [True, False])
+@pytest.mark.parametrize("pad", [0, 1])
+def test_scan_i32_exact(variant, ept, n, inclusive, pad):
+    import torch
+    sk = skel()
+    x = syn.uniform_int(syn.SEED_INT + n, n, 0, 100)
+    dx = dev_tensor(x, pad)
+    dout = dev_empty((n,), torch.int32, pad)
+    with forced("scan", variant, 0, ept):
+        sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
+    assert np.array_equal(to_np(dout), mod32(oracle.scan_i32(x, inclusive)))
+
+
+@pytest.mark.parametrize("variant,ept", SCAN_CONFIGS)
+@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_f32(variant, ept, n, inclusive):
+    import torch
+    sk = skel()
+    x = syn.uniform_f32(syn.SEED_X + n, n)
+    dx = dev_tensor(x)
+    dout = dev_empty((n,), torch.float32)
+    with forced("scan", variant, 0, ept):
+        sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
+    ref, ab = oracle.scan_f32(x, inclusive)
+    assert_prefix_close(to_np(dout), ref, ab, f"scan f32 n={n} incl={inclusive}")
+
+
+def test_scan_i32_wraps_modulo_2pow32():
+    import torch
+    sk = skel()
+    n = 100_000
+    x = syn.uniform_int(5, n, 2**30, 2**31 - 1)
+    dout = dev_empty((n,), torch.int32)
+    for variant in (0, 1, 2):
+        with forced("scan", variant):
+            sk.skel_scan("add", True, wrap(dev_tensor(x)), wrap(dout))
+        assert np.array_equal(to_np(dout), mod32(oracle.scan_i32(x, True)))
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("rows,cols", [(1, 1), (5, 1), (3, 5000), (7, 4096), (4, 4097), (64, 1000)])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_rows(variant, rows, cols, inclusive):
+    """A 2D container is scanned along each row independently."""
+    import torch
+    sk = skel()
+    x = syn.uniform_f32(41, rows * cols).reshape(rows, cols)
+    xi = syn.uniform_int(42, rows * cols, 0, 100).reshape(rows, cols)
+    dout = dev_empty((rows, cols), torch.float32)
+    douti = dev_empty((rows, cols), torch.int32)
+    with forced("scan", variant):
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(x)), wrap(dout))
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xi)), wrap(douti))
+    g, gi = to_np(dout), to_np(douti)
+    for r in range(rows):
+        ref, ab = oracle.scan_f32(x[r], inclusive)
+        assert_prefix_close(g[r], ref, ab, f"row {r}")
+        assert np.array_equal(gi[r], mod32(oracle.scan_i32(xi[r], inclusive)))
+
+
+def test_scan_lookback_repeated_runs_identical_int():
+    """Races in the look-back would show up as run-to-run differences."""
+    import torch
+    sk = skel()
+    n = (1 << 22) + 17
+    x = syn.uniform_int(7, n, 0, 100)
+    dx = wrap(dev_tensor(x))
+    ref = mod32(oracle.scan_i32(x, True))
+    dout = dev_empty((n,), torch.int32)
+    with forced("scan", 1):
+        for _ in range(20):
+            dout.fill_(-1)
+            sk.skel_scan("add", True, dx, wrap(dout))
+            assert np.array_equal(to_np(dout), ref)
