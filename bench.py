@@ -1,0 +1,482 @@
+"""Benchmark of the skeleton hot path on GB300.
+
+One step = one pass of every skeleton of the hot path over one batch of
+synthetic input at the size sweep's largest point, n = 2^28 elements
+(float32 / int32, seeded, inputs resident in HBM and each larger than L2):
+
+    map axpy (a = 2.5)            12 B/elem     reduce sum, reduce max   4 B/elem each
+    mapreduce dot                  8 B/elem     scan incl int32, excl f32 8 B/elem each
+    mapoverlap 2D 9pt, 5pt clamp   8 B/point (16384 x 16384 grid, U[0,1])
+    mapoverlap 1D r=8 clamp        8 B/elem     maparray rowdot (16384 x 16384)  4 B/elem
+    maparray gather (A = 2^20)     8 B/elem     batched sumsq + scan (4096 uneven instances) 8 B/elem
+    backward: map tanh 12 B/elem, reverse scan 8 B/elem, transposed 9pt stencil 8 B/point
+
+value = algorithmic bytes of the step / step time (GB/s, whole job over all
+ranks).  Per-skeleton GB/s, the tuned-vs-default speedup, the roofline of
+the dominant kernel, the end-to-end number through host buffers and the
+oracle's CPU throughput are added to the one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+METRIC = "achieved HBM GB/s and fraction of GB300 peak per skeleton; tuned-vs-default-variant speedup"
+N = 1 << 28
+SIDE = 1 << 14
+ROWDOT_M = 1 << 14
+GATHER_M = 1 << 20
+BATCH_B = 4096
+R1D = 8
+TABLE = os.path.join(ROOT, "paper_1405_2915_gb300", "dispatch_gb300.tbl")
+
+
+def workload_config():
+    return {"workload": "skeleton hot path, n = 2^28 per skeleton (grids 16384^2, rowdot 16384x16384, "
+                        "4096 uneven instances in [64, 2^20])",
+            "n": N, "grid": [SIDE, SIDE], "batched_instances": BATCH_B,
+            "l2": "no flush: every input is >= 1 GiB, larger than the 129 MB L2",
+            "parallelism": "replicas (one independent workload per GPU)"}
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                mhz.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+# ---------------------------------------------------------------- workload --
+class Workload:
+    """Inputs (device tensors wrapped as containers) and the step's calls."""
+
+    def __init__(self, sk, torch, rank: int):
+        self.sk, self.torch = sk, torch
+        dev = torch.device("cuda")
+        s = 1000 * rank
+        t0 = time.time()
+        f32 = lambda a: torch.from_numpy(a).to(dev)
+        self.x = f32(syn.uniform_f32(syn.SEED_X + s, N))
+        self.y = f32(syn.uniform_f32(syn.SEED_Y + s, N))
+        self.xi = f32(syn.uniform_int(syn.SEED_INT + s, N, 0, 100))
+        self.grid = f32(syn.uniform_f32(syn.SEED_GRID + s, N, 0.0, 1.0)).view(SIDE, SIDE)
+        self.M = f32(syn.uniform_f32(syn.SEED_MAT + s, N)).view(N // ROWDOT_M, ROWDOT_M)
+        self.A = f32(syn.uniform_f32(syn.SEED_X + s + 7, ROWDOT_M))
+        self.Ag = f32(syn.uniform_f32(syn.SEED_X + s + 8, GATHER_M))
+        self.idx = f32(syn.uniform_int(syn.SEED_IDX + s, N, 0, GATHER_M - 1))
+        lens = syn.loguniform_lengths(syn.SEED_BATCH_LEN + s, BATCH_B)
+        off = syn.csr_offsets(lens)
+        self.total = int(off[-1])
+        self.bv = f32(syn.uniform_f32(syn.SEED_BATCH_VAL + s, self.total))
+        self.boff = f32(off)
+        self.gen_s = time.time() - t0
+        e = lambda shape, dt=torch.float32: torch.empty(shape, dtype=dt, device=dev)
+        self.oA, self.oB = e(N), e(N)
+        self.oI = e(N, torch.int32)
+        self.oG, self.oG2 = e((SIDE, SIDE)), e((SIDE, SIDE))
+        self.rd = e(N // ROWDOT_M)
+        self.bres, self.bsc = e(BATCH_B), e(self.total)
+        self.r1 = e(1)
+        C = sk.Container.from_tensor
+        self.c = {k: C(getattr(self, k)) for k in
+                  ("x", "y", "xi", "grid", "M", "A", "Ag", "idx", "bv", "boff", "oA", "oB", "oI", "oG", "oG2",
+                   "rd", "bres", "bsc", "r1")}
+
+    def calls(self):
+        """(name, algorithmic bytes, thunk) for every call of one step."""
+        sk, c, n = self.sk, self.c, N
+        return [
+            ("map_axpy", 12 * n, lambda: sk.skel_map("axpy", [c["x"], c["y"]], c["oA"], [2.5])),
+            ("reduce_sum", 4 * n, lambda: sk.skel_reduce("add", c["x"], c["r1"], host=False)),
+            ("reduce_max", 4 * n, lambda: sk.skel_reduce("max", c["x"], c["r1"], host=False)),
+            ("mapreduce_dot", 8 * n, lambda: sk.skel_mapreduce("mul", "add", [c["x"], c["y"]], c["r1"], host=False)),
+            ("scan_incl_i32", 8 * n, lambda: sk.skel_scan("add", True, c["xi"], c["oI"])),
+            ("scan_excl_f32", 8 * n, lambda: sk.skel_scan("add", False, c["x"], c["oB"])),
+            ("mapoverlap2d_9pt", 8 * n, lambda: sk.skel_mapoverlap("stencil9", 1, None, "clamp", c["grid"], c["oG"])),
+            ("mapoverlap2d_5pt", 8 * n, lambda: sk.skel_mapoverlap("stencil5", 1, None, "clamp", c["grid"], c["oG2"])),
+            ("mapoverlap1d_r8", 8 * n, lambda: sk.skel_mapoverlap("stencil1d", R1D, None, "clamp", c["x"], c["oA"])),
+            ("maparray_rowdot", 4 * n + 4 * ROWDOT_M + 4 * (n // ROWDOT_M),
+             lambda: sk.skel_maparray("rowdot", c["A"], c["M"], c["rd"])),
+            ("maparray_gather", 8 * n, lambda: sk.skel_maparray("gather", c["Ag"], c["idx"], c["oB"])),
+            ("batched_sumsq_scan", 8 * self.total + 8 * (BATCH_B + 1) + 4 * BATCH_B,
+             lambda: sk.skel_batched(c["bv"], c["boff"], c["bres"], c["bsc"], True)),
+            ("map_tanh_bwd", 12 * n, lambda: sk.skel_map_bwd("tanh", [c["y"]], c["x"], [c["oA"]], [1.0])),
+            ("scan_bwd_f32", 8 * n, lambda: sk.skel_scan_bwd("add", True, c["x"], c["oB"])),
+            ("mapoverlap2d_9pt_bwd", 8 * n, lambda: sk.skel_mapoverlap_bwd("stencil9", 1, None, "clamp", c["grid"], c["oG"])),
+        ]
+
+
+def run_steps(torch, calls, steps, stream, per_call=True):
+    """Runs `steps` steps; returns (total ms, {name: summed ms})."""
+    E = torch.cuda.Event
+    if per_call:
+        evs = [[E(enable_timing=True) for _ in range(len(calls) + 1)] for _ in range(steps)]
+    start, end = E(enable_timing=True), E(enable_timing=True)
+    start.record(stream)
+    for s in range(steps):
+        if per_call:
+            evs[s][0].record(stream)
+        for k, (_, _, fn) in enumerate(calls):
+            fn()
+            if per_call:
+                evs[s][k + 1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    per = {}
+    if per_call:
+        for k, (name, _, _) in enumerate(calls):
+            per[name] = sum(evs[s][k].elapsed_time(evs[s][k + 1]) for s in range(steps))
+    return start.elapsed_time(end), per
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def committed_traffic(kernel_key: str):
+    """dram bytes per launch of a kernel from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 2 and not line.startswith("#") and parts[0] == kernel_key:
+            return float(parts[1])
+    return None
+
+
+# ------------------------------------------------------------- CPU oracle --
+def oracle_sample_step(sample: int):
+    """One bounded sample of the step on the host: every skeleton of the step
+    run by the float64 oracle on `sample` elements.  Returns (seconds, bytes),
+    the bytes counted with the same per-element figures as the GPU step."""
+    import oracle
+    n = sample
+    side = int(np.sqrt(n))
+    x, y = syn.uniform_f32(syn.SEED_X, n), syn.uniform_f32(syn.SEED_Y, n)
+    xi = syn.uniform_int(syn.SEED_INT, n, 0, 100)
+    g = syn.uniform_f32(syn.SEED_GRID, side * side, 0.0, 1.0).reshape(side, side)
+    m = 1 << 10
+    M = syn.uniform_f32(syn.SEED_MAT, (n // m) * m).reshape(n // m, m)
+    A = syn.uniform_f32(syn.SEED_X + 7, m)
+    Ag = syn.uniform_f32(syn.SEED_X + 8, GATHER_M)
+    idx = syn.uniform_int(syn.SEED_IDX, n, 0, GATHER_M - 1)
+    lens = syn.loguniform_lengths(syn.SEED_BATCH_LEN, 64, 64, 1 << 16)
+    off = syn.csr_offsets(lens)
+    bv = syn.uniform_f32(syn.SEED_BATCH_VAL, int(off[-1]))
+    w9, w5 = oracle.stencil_weights("9pt"), oracle.stencil_weights("5pt")
+    # the library's default 1D weights: binomial C(2r, k) / 4^r
+    w1 = (np.array([math.comb(2 * R1D, k) for k in range(2 * R1D + 1)], np.float64) / 4 ** R1D).astype(np.float32)
+    t0 = time.perf_counter()
+    oracle.map_f32("axpy", x, y, a=2.5)
+    oracle.reduce_f32("add", x)
+    oracle.reduce_f32("max", x)
+    oracle.mapreduce_f32("mul", x, y)
+    oracle.scan_i32(xi, True)
+    oracle.scan_f32(x, False)
+    oracle.mapoverlap2d_f32(g, 1, w9, "clamp")
+    oracle.mapoverlap2d_f32(g, 1, w5, "clamp")
+    oracle.mapoverlap1d_f32(x, R1D, w1, "clamp")
+    oracle.rowdot_f32(A, M)
+    oracle.gather_f32(Ag, idx)
+    oracle.batched_f32(bv, off, True)
+    oracle.map_bwd_f32("tanh", x, y)
+    oracle.scan_bwd_f32(x, True)
+    oracle.mapoverlap2d_bwd_f32(g, 1, w9, "clamp")
+    dt = time.perf_counter() - t0
+    nb = (12 + 4 + 4 + 8 + 8 + 8 + 8 + 8 + 8 + 4 + 8 + 12 + 8 + 8) * n + 8 * int(off[-1])
+    return dt, nb
+
+
+def reference_sample(n_steps: int, budget_s: float = 150.0, cap_s: float = 8.0) -> int:
+    """Elements per sampled step so that n_steps oracle steps take about
+    min(cap_s, budget_s / n_steps) seconds each (a power of two in [2^16, 2^26])."""
+    t1, _ = oracle_sample_step(1 << 18)
+    target = min(cap_s, budget_s / max(1, n_steps))
+    k = int(np.clip(np.floor(np.log2(max(target / max(t1, 1e-6), 1e-3))) + 18, 16, 26))
+    return 1 << k
+
+
+def cpu_baseline(sample: int = 1 << 25):
+    dt, nb = oracle_sample_step(sample)
+    return {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"every skeleton of the step on n = {sample} elements (float64 oracle, one thread), "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample = reference_sample(args.steps + args.warmup)
+    for _ in range(args.warmup):
+        oracle_sample_step(sample)
+    tot_t = tot_b = 0.0
+    for _ in range(args.steps):
+        dt, nb = oracle_sample_step(sample)
+        tot_t += dt
+        tot_b += nb
+    value = tot_b / tot_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: every skeleton of the step on n = {sample} elements "
+                                       "(float64 oracle, one thread)"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- e2e ----
+def e2e_run(sk, torch, steps, stream):
+    """The same step through the public API with host buffers: inputs live in
+    pinned host memory and are copied lazily by the containers (H2D inside
+    the timed region), results are read back to the host (D2H)."""
+    dev = torch.device("cuda")
+    pin = lambda a: torch.from_numpy(a).pin_memory()
+    h = {}
+    h["x"] = pin(syn.uniform_f32(syn.SEED_X, N))
+    h["y"] = pin(syn.uniform_f32(syn.SEED_Y, N))
+    h["xi"] = pin(syn.uniform_int(syn.SEED_INT, N, 0, 100))
+    h["grid"] = pin(syn.uniform_f32(syn.SEED_GRID, N, 0.0, 1.0).reshape(SIDE, SIDE))
+    h["M"] = pin(syn.uniform_f32(syn.SEED_MAT, N).reshape(N // ROWDOT_M, ROWDOT_M))
+    h["A"] = pin(syn.uniform_f32(syn.SEED_X + 7, ROWDOT_M))
+    h["Ag"] = pin(syn.uniform_f32(syn.SEED_X + 8, GATHER_M))
+    h["idx"] = pin(syn.uniform_int(syn.SEED_IDX, N, 0, GATHER_M - 1))
+    lens = syn.loguniform_lengths(syn.SEED_BATCH_LEN, BATCH_B)
+    off = syn.csr_offsets(lens)
+    total = int(off[-1])
+    h["bv"] = pin(syn.uniform_f32(syn.SEED_BATCH_VAL, total))
+    h["boff"] = pin(off)
+    C = sk.Container
+    ci = {k: C.from_host(v.numpy()) for k, v in h.items()}
+    outs = {"oA": (N,), "oB": (N,), "oG": (SIDE, SIDE), "oG2": (SIDE, SIDE), "rd": (N // ROWDOT_M,),
+            "bres": (BATCH_B,), "bsc": (total,), "r1": (1,)}
+    co = {k: C.empty(s) for k, s in outs.items()}
+    co["oI"] = C.empty((N,), np.int32)
+    c = {**ci, **co}
+    calls = [
+        lambda: sk.skel_map("axpy", [c["x"], c["y"]], c["oA"], [2.5]),
+        lambda: sk.skel_reduce("add", c["x"], c["r1"], host=False),
+        lambda: sk.skel_reduce("max", c["x"], c["r1"], host=False),
+        lambda: sk.skel_mapreduce("mul", "add", [c["x"], c["y"]], c["r1"], host=False),
+        lambda: sk.skel_scan("add", True, c["xi"], c["oI"]),
+        lambda: sk.skel_scan("add", False, c["x"], c["oB"]),
+        lambda: sk.skel_mapoverlap("stencil9", 1, None, "clamp", c["grid"], c["oG"]),
+        lambda: sk.skel_mapoverlap("stencil5", 1, None, "clamp", c["grid"], c["oG2"]),
+        lambda: sk.skel_mapoverlap("stencil1d", R1D, None, "clamp", c["x"], c["oA"]),
+        lambda: sk.skel_maparray("rowdot", c["A"], c["M"], c["rd"]),
+        lambda: sk.skel_maparray("gather", c["Ag"], c["idx"], c["oB"]),
+        lambda: sk.skel_batched(c["bv"], c["boff"], c["bres"], c["bsc"], True),
+        lambda: sk.skel_map_bwd("tanh", [c["y"]], c["x"], [c["oA"]], [1.0]),
+        lambda: sk.skel_scan_bwd("add", True, c["x"], c["oB"]),
+        lambda: sk.skel_mapoverlap_bwd("stencil9", 1, None, "clamp", c["grid"], c["oG"]),
+    ]
+    read_back = ["oA", "oB", "oI", "oG", "oG2", "rd", "bres", "bsc", "r1"]
+
+    def one_step():
+        for k in ci:                       # the host copies hold this step's inputs
+            ci[k].mark(sk.UNIT_HOST)
+        for fn in calls:
+            fn()
+        for k in read_back:                # results to the host
+            c[k].host_ptr(sk.READ, stream)
+
+    def stats():
+        hs = [c[k].stats() for k in c]
+        return sum(s["h2d_bytes"] for s in hs), sum(s["d2h_bytes"] for s in hs)
+
+    one_step()                             # warm-up (allocates device and pinned copies)
+    b0 = stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    b1 = stats()
+    for v in c.values():
+        v.close()
+    return dt, (b1[0] - b0[0]) / steps, (b1[1] - b0[1]) / steps
+
+
+# -------------------------------------------------------------------- main --
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1405_2915_gb300 as sk
+
+    tuned = os.path.exists(TABLE)
+    if tuned:
+        sk.skel_load_dispatch_table(TABLE)
+    wl = Workload(sk, torch, rank)
+    calls = wl.calls()
+    stream = torch.cuda.current_stream()
+    step_bytes = sum(b for _, b, _ in calls)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+
+    # warm-up, then the timed region (per-call events on the launching stream)
+    run_steps(torch, calls, args.warmup, stream, per_call=False)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.2)
+    barrier()
+    l0 = sk.lib.skel_launch_count()
+    total_ms, per = run_steps(torch, calls, args.steps, stream)
+    launches = sk.lib.skel_launch_count() - l0
+    barrier()
+    clocks = sampler.stop()
+    sk.skel_check_device()
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    ms_step = t_max / args.steps
+    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+
+    # the fixed default variants (empty table), same steps
+    sk.skel_load_dispatch_table(None)
+    run_steps(torch, calls, 3, stream, per_call=False)
+    barrier()
+    def_ms, per_def = run_steps(torch, calls, args.steps, stream)
+    barrier()
+    if tuned:
+        sk.skel_load_dispatch_table(TABLE)
+
+    hbm, peak_kind = peaks()
+    per_sk = {}
+    for name, b, _ in calls:
+        ms = per[name] / args.steps
+        gbs = b / (ms * 1e-3) / 1e9
+        per_sk[name] = {"GB/s": round(gbs, 1), "frac": round(gbs / hbm, 3), "ms": round(ms, 4),
+                        "default_ms": round(per_def[name] / args.steps, 4),
+                        "tuned_vs_default": round(per_def[name] / per[name], 3)}
+    dom = max(calls, key=lambda c: per[c[0]])
+    dom_ms = per[dom[0]] / args.steps
+    dom_gbs = dom[1] / (dom_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(dom_gbs, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(dom_gbs / hbm, 3), "peak_kind": peak_kind,
+                "traffic": committed_traffic(dom[0])}
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(),
+            "frac_of_peak": round(value / world / hbm, 3),
+            "tuned_vs_default_speedup": round(def_ms / total_ms, 3), "dispatch_table": tuned,
+            "per_skeleton": per_sk, "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+            "input_gen_s": round(wl.gen_s, 1)}
+    del wl, calls
+    torch.cuda.empty_cache()
+    if not args.no_e2e:
+        dt, h2d, d2h = e2e_run(sk, torch, min(args.steps, 3), stream)
+        line["e2e"] = {"value": round(world * step_bytes / dt / 1e9, 1), "unit": "GB/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": round(dt * 1e3, 2)}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -137,9 +137,13 @@ const char *skel_last_error(void);
 int skel_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
                        void (*free_fn)(void *ptr, void *stream, void *ctx), void *ctx);
 
-/* Releases the cached scratch memory of every stream and the library's
- * pinned staging buffers.  Containers are not touched. */
+/* Releases the cached scratch memory and result slots of every stream.
+ * Containers are not touched.  Waits for the streams that used them. */
 int skel_release_cached(void);
+
+/* Number of CUDA kernels the library has launched in this process (all
+ * threads, all devices); a skeleton call launches one to four. */
+int64_t skel_launch_count(void);
 
 /* ------------------------------------------------ smart containers (IV) --- */
 

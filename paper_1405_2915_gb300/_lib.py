@@ -34,6 +34,7 @@ SIGNATURES = {
     "skel_last_error": (C.c_char_p, []),
     "skel_set_allocator": (i32, [ALLOC_FN, FREE_FN, vp]),
     "skel_release_cached": (i32, []),
+    "skel_launch_count": (i64, []),
     "skel_container_create": (i32, [i32, i32, C.POINTER(i64), C.POINTER(vp)]),
     "skel_container_wrap": (i32, [i32, i32, C.POINTER(i64), vp, vp, i32, C.POINTER(vp)]),
     "skel_container_view": (i32, [vp, i64, i32, C.POINTER(i64), C.POINTER(vp)]),

@@ -198,6 +198,8 @@ int skel_set_allocator(void *(*alloc)(size_t, void *, void *), void (*free_fn)(v
 
 int skel_release_cached(void) { return guarded([&] { return release_scratch(); }); }
 
+int64_t skel_launch_count(void) { return launch_count(); }
+
 int skel_coherence_step(int valid_units, int unit, int mode, int *new_valid, int *transfer)
 {
     return guarded([&] {

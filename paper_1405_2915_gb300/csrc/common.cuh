@@ -145,6 +145,16 @@ __device__ __forceinline__ float4 map4_apply(float4 x, float4 y, float a,
 
 // Host helpers ------------------------------------------------------------
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Every kernel of the library is launched through this wrapper, which
+// counts launches (skel_launch_count).
+template <class... KArgs, class... Args>
+inline void launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args &&...args)
+{
+    kernel<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+    note_launch();
+}
 inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 }  // namespace skel

@@ -22,6 +22,10 @@ int fail_cuda(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return ::skel::fail_cuda(e_, #expr); \
     } while (0)
 
+// Process-wide count of kernel launches made by the library.
+void note_launch();
+int64_t launch_count();
+
 // ---------------------------------------------------------------- device --
 struct DeviceInfo {
     int device;

@@ -236,7 +236,7 @@ int run_main(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *fl
     if (grid < 1) grid = 1;
     if (grid > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "batched: too many tiles");
     const DebugKnobs k = debug_knobs();
-    kern<<<(unsigned)grid, kBlock, 0, s>>>(b.values, b.offsets, b.results, b.scan_out, L, flags, ctl, epoch,
+    launch_kernel(kern, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.results, b.scan_out, L, flags, ctl, epoch,
                                            k.wait_limit_ns);
     cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "batched launch");
@@ -250,7 +250,7 @@ int run_v(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags
     const Layout L = layout(data, b, TILE);
     const int64_t mt = max_tiles(b, TILE);
     if (mt > 0x7fffffffLL || b.B > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "batched: too many instances or tiles");
-    batched_prep<<<1, 1024, 0, s>>>(b.offsets, b.B, b.total, TILE, L, b.results, ctl, mt);
+    launch_kernel(batched_prep, 1, 1024, 0, s, b.offsets, b.B, b.total, TILE, L, b.results, ctl, mt);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prep launch");
     if (b.want_scan && b.want_reduce)

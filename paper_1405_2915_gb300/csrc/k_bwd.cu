@@ -86,8 +86,8 @@ int run(const BwdArgs &p, cudaStream_t s)
     const int64_t cap = (int64_t)device_info().sms * 8 * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    if (vec) map_bwd_kernel<FN, true><<<(unsigned)grid, 256, 0, s>>>(p);
-    else map_bwd_kernel<FN, false><<<(unsigned)grid, 256, 0, s>>>(p);
+    if (vec) launch_kernel(map_bwd_kernel<FN, true>, (unsigned)grid, 256, 0, s, p);
+    else launch_kernel(map_bwd_kernel<FN, false>, (unsigned)grid, 256, 0, s, p);
     cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "map backward launch");
 }

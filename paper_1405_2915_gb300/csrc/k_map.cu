@@ -122,7 +122,7 @@ int run_map(const MapLaunch &m, const Choice &c, cudaStream_t s)
         const int64_t cap = (int64_t)device_info().sms * (2048 / block) * 4;
         if (grid > cap) grid = cap;
         if (grid < 1) grid = 1;
-        map_scalar<FN><<<(unsigned)grid, block, 0, s>>>(m.in0, m.in1, m.out, m.n, a);
+        launch_kernel(map_scalar<FN>, (unsigned)grid, block, 0, s, m.in0, m.in1, m.out, m.n, a);
         return cudaPeekAtLastError() == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "map_scalar");
     }
     // vectorised variants: same offset modulo 16 bytes for every operand
@@ -148,9 +148,9 @@ int run_map(const MapLaunch &m, const Choice &c, cudaStream_t s)
     const unsigned g = (unsigned)grid;
 #define SKEL_MAP_EPT(E)                                                                          \
     do {                                                                                         \
-        if (c.variant == 1) map_vec<FN, E, false><<<g, block, 0, s>>>(m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
-        else if (c.variant == 2) map_vec<FN, E, true><<<g, block, 0, s>>>(m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
-        else map_vec_grid<FN, E><<<g, block, 0, s>>>(m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
+        if (c.variant == 1) launch_kernel(map_vec<FN, E, false>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
+        else if (c.variant == 2) launch_kernel(map_vec<FN, E, true>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
+        else launch_kernel(map_vec_grid<FN, E>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
     } while (0)
     switch (ept) {
     case 1: SKEL_MAP_EPT(1); break;

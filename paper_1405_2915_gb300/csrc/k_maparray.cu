@@ -144,13 +144,13 @@ int launch_maparray(const MapArrayLaunch &ma, const Choice &c, cudaStream_t s)
     if (ma.fn == SKEL_FN_GATHER) {
         const int32_t *idx = static_cast<const int32_t *>(ma.B);
         if (c.variant == 0) {
-            gather_scalar<<<grid_for(ma.n, block), block, 0, s>>>(ma.A, ma.m, idx, ma.out, ma.n);
+            launch_kernel(gather_scalar, grid_for(ma.n, block), block, 0, s, ma.A, ma.m, idx, ma.out, ma.n);
             return check_launch("gather scalar");
         }
         if (c.variant == 1) {
             if (!aligned16(idx) || !aligned16(ma.out))
                 return fail(SKEL_ERR_UNSUPPORTED, "gather vec4: 16-byte aligned operands needed");
-            gather_vec4<<<grid_for(ceil_div(ma.n, 4), block), block, 0, s>>>(ma.A, ma.m, idx, ma.out, ma.n);
+            launch_kernel(gather_vec4, grid_for(ceil_div(ma.n, 4), block), block, 0, s, ma.A, ma.m, idx, ma.out, ma.n);
             return check_launch("gather vec4");
         }
         return fail(SKEL_ERR_UNSUPPORTED, "gather: variant not offered");
@@ -159,21 +159,21 @@ int launch_maparray(const MapArrayLaunch &ma, const Choice &c, cudaStream_t s)
         const float *M = static_cast<const float *>(ma.B);
         const bool vec = aligned16(M) && aligned16(ma.A) && ma.m % 4 == 0;
         if (c.variant == 0) {
-            rowdot_thread<<<grid_for(ma.n, block), block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            launch_kernel(rowdot_thread, grid_for(ma.n, block), block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
             return check_launch("rowdot thread");
         }
         if (c.variant == 1) {
             const unsigned g = grid_for(ceil_div(ma.n, 8) * 256, block);
-            if (vec) rowdot_warp<true><<<g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
-            else rowdot_warp<false><<<g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            if (vec) launch_kernel(rowdot_warp<true>, g, block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
+            else launch_kernel(rowdot_warp<false>, g, block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
             return check_launch("rowdot warp");
         }
         if (c.variant == 2) {
             int64_t g = ma.n;
             const int64_t cap = (int64_t)device_info().sms * 8 * 16;
             if (g > cap) g = cap;
-            if (vec) rowdot_block<true><<<(unsigned)g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
-            else rowdot_block<false><<<(unsigned)g, block, 0, s>>>(ma.A, ma.m, M, ma.out, ma.n);
+            if (vec) launch_kernel(rowdot_block<true>, (unsigned)g, block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
+            else launch_kernel(rowdot_block<false>, (unsigned)g, block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
             return check_launch("rowdot block");
         }
         return fail(SKEL_ERR_INVALID_ARG, "rowdot: unknown variant");

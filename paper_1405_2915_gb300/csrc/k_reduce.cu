@@ -182,7 +182,7 @@ int run_reduce_block(const ReduceLaunch &r, const Choice &c, cudaStream_t s)
         ctl = scr.ctl;
     }
     const int single = c.variant == 1 ? 1 : 0;
-#define SKEL_RED_EPT(E) reduce_phase1<Op, MAPF, NIN, E, BLOCK, T><<<(unsigned)grid, BLOCK, 0, s>>>(x, y, r.n, sp, partials, out, ctl, single)
+#define SKEL_RED_EPT(E) launch_kernel(reduce_phase1<Op, MAPF, NIN, E, BLOCK, T>, (unsigned)grid, BLOCK, 0, s, x, y, r.n, sp, partials, out, ctl, single)
     switch (ept) {
     case 1: SKEL_RED_EPT(1); break;
     case 2: SKEL_RED_EPT(2); break;
@@ -192,7 +192,7 @@ int run_reduce_block(const ReduceLaunch &r, const Choice &c, cudaStream_t s)
     }
 #undef SKEL_RED_EPT
     if (c.variant == 0 && grid > 1)
-        reduce_phase2<Op, BLOCK, T><<<1, BLOCK, 0, s>>>(partials, (int)grid, out);
+        launch_kernel(reduce_phase2<Op, BLOCK, T>, 1, BLOCK, 0, s, partials, (int)grid, out);
     cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "reduce launch");
 }
@@ -229,9 +229,9 @@ int launch_reduce(const ReduceLaunch &r, const Choice &c, cudaStream_t s)
     if (c.variant < 0 || c.variant > 2) return fail(SKEL_ERR_INVALID_ARG, "reduce: unknown variant");
     if (r.n == 0) {
         if (r.dtype == SKEL_F32)
-            write_scalar<float><<<1, 1, 0, s>>>((float *)r.out, r.op == SKEL_FN_MAX ? -INFINITY : 0.f);
+            launch_kernel(write_scalar<float>, 1, 1, 0, s, (float *)r.out, r.op == SKEL_FN_MAX ? -INFINITY : 0.f);
         else
-            write_scalar<uint32_t><<<1, 1, 0, s>>>((uint32_t *)r.out, r.op == SKEL_FN_MAX ? 0x80000000u : 0u);
+            launch_kernel(write_scalar<uint32_t>, 1, 1, 0, s, (uint32_t *)r.out, r.op == SKEL_FN_MAX ? 0x80000000u : 0u);
         cudaError_t e = cudaPeekAtLastError();
         return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "reduce identity");
     }

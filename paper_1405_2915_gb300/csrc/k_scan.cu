@@ -200,15 +200,15 @@ int run_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
     g.vec_ok = ptr_ok && seg_ok;
     if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
     if (c.variant == 2) {
-        scan_one_block<T, INCL, V><<<1, kBlock, 0, s>>>(in, out, g);
+        launch_kernel(scan_one_block<T, INCL, V>, 1, kBlock, 0, s, in, out, g);
     } else if (c.variant == 0) {
         Scratch scr{};
         int rc = get_scratch(s, (size_t)g.ntiles * sizeof(CT), 0, &scr);
         if (rc) return rc;
         CT *sums = reinterpret_cast<CT *>(scr.data);
-        scan_tile_sums<T, V><<<(unsigned)g.ntiles, kBlock, 0, s>>>(in, g, sums);
-        scan_tile_prefixes<CT><<<(unsigned)(g.ntiles / g.tps), 1024, 0, s>>>(sums, g.tps);
-        scan_tile_apply<T, INCL, V><<<(unsigned)g.ntiles, kBlock, 0, s>>>(in, out, g, sums);
+        launch_kernel(scan_tile_sums<T, V>, (unsigned)g.ntiles, kBlock, 0, s, in, g, sums);
+        launch_kernel(scan_tile_prefixes<CT>, (unsigned)(g.ntiles / g.tps), 1024, 0, s, sums, g.tps);
+        launch_kernel(scan_tile_apply<T, INCL, V>, (unsigned)g.ntiles, kBlock, 0, s, in, out, g, sums);
     } else {
         Scratch scr{};
         const size_t vb = ((size_t)g.ntiles * sizeof(CT) + 255) & ~(size_t)255;
@@ -219,7 +219,7 @@ int run_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
         d.aggs = reinterpret_cast<CT *>(scr.data);
         d.incls = reinterpret_cast<CT *>(scr.data + vb);
         const DebugKnobs k = debug_knobs();
-        scan_lookback<T, INCL, V><<<(unsigned)g.ntiles, kBlock, 0, s>>>(
+        launch_kernel(scan_lookback<T, INCL, V>, (unsigned)g.ntiles, kBlock, 0, s, 
             in, out, g, d, scr.ctl, scr.epoch, k.scan_skip_publish_tile, k.wait_limit_ns);
     }
     cudaError_t e = cudaPeekAtLastError();

@@ -406,14 +406,14 @@ int run2d(const StencilLaunch &st, const Choice &c, const float *in, float *out,
         return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap 2D: tiled variants need cols % 4 == 0 and 16-byte aligned grids");
     if (c.variant == 0) {
         const int64_t gy = ceil_div(rows, 8);
-        st2_direct<TAPS5><<<dim3((unsigned)ceil_div(cols, 32), (unsigned)(gy < 65535 ? gy : 65535)), 256, 0, s>>>(
+        launch_kernel(st2_direct<TAPS5>, dim3((unsigned)ceil_div(cols, 32), (unsigned)(gy < 65535 ? gy : 65535)), 256, 0, s,
             in, out, rows, cols, b, w);
         return check_launch("mapoverlap2d direct");
     }
     if (ceil_div(rows, kTY) > 65535) return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap 2D: too many tile rows");
     const dim3 grid((unsigned)ceil_div(cols, kTX), (unsigned)ceil_div(rows, kTY));
     if (c.variant == 1) {
-        st2_smem<TAPS5><<<grid, 256, 0, s>>>(in, out, rows, cols, b, w);
+        launch_kernel(st2_smem<TAPS5>, grid, 256, 0, s, in, out, rows, cols, b, w);
         return check_launch("mapoverlap2d smem");
     }
     if (c.variant == 2) {
@@ -433,7 +433,7 @@ int run2d(const StencilLaunch &st, const Choice &c, const float *in, float *out,
         int rc = get_scratch(s, 0, 0, &scr);
         if (rc) return rc;
         const int smem = kSH * kSW * 4 + 16;   // tile + mbarrier
-        st2_tma<TAPS5><<<grid, 256, smem, s>>>(map, in, out, rows, cols, b, w, scr.ctl);
+        launch_kernel(st2_tma<TAPS5>, grid, 256, smem, s, map, in, out, rows, cols, b, w, scr.ctl);
         return check_launch("mapoverlap2d tma");
     }
     if (c.variant == 3) {
@@ -442,10 +442,10 @@ int run2d(const StencilLaunch &st, const Choice &c, const float *in, float *out,
         if (gy > 65535) return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap 2D: too many row segments");
         const dim3 g2((unsigned)ceil_div(cols, 512), (unsigned)gy);
         switch (rh) {
-        case 16: st2_colwalk<TAPS5, 16><<<g2, 128, 0, s>>>(in, out, rows, cols, b, w); break;
-        case 32: st2_colwalk<TAPS5, 32><<<g2, 128, 0, s>>>(in, out, rows, cols, b, w); break;
-        case 64: st2_colwalk<TAPS5, 64><<<g2, 128, 0, s>>>(in, out, rows, cols, b, w); break;
-        case 128: st2_colwalk<TAPS5, 128><<<g2, 128, 0, s>>>(in, out, rows, cols, b, w); break;
+        case 16: launch_kernel(st2_colwalk<TAPS5, 16>, g2, 128, 0, s, in, out, rows, cols, b, w); break;
+        case 32: launch_kernel(st2_colwalk<TAPS5, 32>, g2, 128, 0, s, in, out, rows, cols, b, w); break;
+        case 64: launch_kernel(st2_colwalk<TAPS5, 64>, g2, 128, 0, s, in, out, rows, cols, b, w); break;
+        case 128: launch_kernel(st2_colwalk<TAPS5, 128>, g2, 128, 0, s, in, out, rows, cols, b, w); break;
         default: return fail(SKEL_ERR_INVALID_ARG, "column_walk: tile (rows per walk) must be 16, 32, 64 or 128");
         }
         return check_launch("mapoverlap2d column_walk");
@@ -460,13 +460,13 @@ int run1d_r(const Choice &c, const float *in, float *out, int64_t n, int b, cons
         int64_t grid = ceil_div(n, 256);
         const int64_t cap = (int64_t)device_info().sms * 32;
         if (grid > cap) grid = cap;
-        st1_direct<R><<<(unsigned)grid, 256, 0, s>>>(in, out, n, b, w);
+        launch_kernel(st1_direct<R>, (unsigned)grid, 256, 0, s, in, out, n, b, w);
         return check_launch("mapoverlap1d direct");
     }
     if (c.variant == 1) {
         const int64_t grid = ceil_div(n, k1Tile);
         if (grid > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "mapoverlap1d: too long");
-        st1_smem<R><<<(unsigned)grid, 256, 0, s>>>(in, out, n, b, w);
+        launch_kernel(st1_smem<R>, (unsigned)grid, 256, 0, s, in, out, n, b, w);
         return check_launch("mapoverlap1d smem");
     }
     return fail(SKEL_ERR_INVALID_ARG, "mapoverlap 1D: unknown variant");
@@ -511,8 +511,8 @@ int launch_stencil(const StencilLaunch &st, const Choice &c, cudaStream_t s)
         const int64_t nb = st.rows * st.cols;   // upper bound of border cells
         int64_t grid = ceil_div(nb < 4 * (st.rows + st.cols) ? nb : 4 * (st.rows + st.cols), 256);
         if (grid > 4096) grid = 4096;
-        if (st.taps5) st2_fold_border<true><<<(unsigned)grid, 256, 0, s>>>(st.in, st.out, st.rows, st.cols, w);
-        else st2_fold_border<false><<<(unsigned)grid, 256, 0, s>>>(st.in, st.out, st.rows, st.cols, w);
+        if (st.taps5) launch_kernel(st2_fold_border<true>, (unsigned)grid, 256, 0, s, st.in, st.out, st.rows, st.cols, w);
+        else launch_kernel(st2_fold_border<false>, (unsigned)grid, 256, 0, s, st.in, st.out, st.rows, st.cols, w);
         return check_launch("mapoverlap2d adjoint border");
     }
     W33 w{}, wf{};
@@ -523,7 +523,7 @@ int launch_stencil(const StencilLaunch &st, const Choice &c, cudaStream_t s)
     }
     int rc = run1d(c, r, st.in, st.out, st.cols, b, wf, s);
     if (rc || !st.transpose || st.boundary != SKEL_CLAMP || r == 0) return rc;
-    st1_fold_ends<<<1, 32, 0, s>>>(st.in, st.out, st.cols, r, w);
+    launch_kernel(st1_fold_ends, 1, 32, 0, s, st.in, st.out, st.cols, r, w);
     return check_launch("mapoverlap1d adjoint ends");
 }
 

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -38,6 +39,11 @@ int fail_cuda(cudaError_t e, const char *what)
 
 const char *last_error_cstr() { return g_last_error.c_str(); }
 void clear_error() { g_last_error.clear(); }
+
+// ---------------------------------------------------------------- launches --
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 // ------------------------------------------------------------------ device --
 const DeviceInfo &device_info()

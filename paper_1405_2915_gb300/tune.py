@@ -1,0 +1,379 @@
+"""Off-line autotuner: builds the execution-plan table (Sec. II off-line
+tuning into a dispatch structure for fast run-time lookup; Sec. III execution
+plans recomputed once per target system) by timing every variant and launch
+shape of each skeleton instance at one representative size per bucket
+(n = 4^k, bucket k = floor(log2(n) / 2)).
+
+Rules:
+  * the built-in default variant is always a candidate, and another candidate
+    replaces it only when it is faster by more than `--margin` (3 %);
+  * each candidate is timed on the device (CUDA events on the launching
+    stream) as the median of `--reps` runs, with L2 flushed before every run
+    when the operands fit in L2;
+  * after tuning, sizes between the buckets (n = 2 * 4^k) are timed with the
+    table and with the defaults, to check that the table is never slower.
+
+    python -m paper_1405_2915_gb300.tune --out paper_1405_2915_gb300/dispatch_gb300.tbl \
+        --report profiles/sweep_tuned_vs_default_gb300.md
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import os
+import statistics
+import sys
+import time
+
+import numpy as np
+import torch
+
+from . import (F32, I32, SK, Container, SkelError, skel_batched, skel_force_variant, skel_load_dispatch_table,
+               skel_map, skel_mapoverlap, skel_maparray, skel_mapreduce, skel_reduce, skel_scan)
+from ._lib import FN
+
+L2_FLUSH_BYTES = 512 << 20
+
+
+class Timer:
+    def __init__(self):
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.stream = torch.cuda.current_stream()
+
+    def time(self, fn, nbytes: int, reps: int) -> float:
+        """Median device time in ms of fn()."""
+        fn()   # warm-up (also surfaces an unsupported configuration)
+        flush = nbytes < 2 * 129 * (1 << 20)
+        ts = []
+        for _ in range(reps):
+            if flush:
+                self.flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+
+def grid_of(**axes):
+    keys = list(axes)
+    for vals in itertools.product(*(axes[k] for k in keys)):
+        yield dict(zip(keys, vals))
+
+
+# candidates per skeleton: (variant, block, ept, tile)
+def candidates(sk_name: str):
+    if sk_name == "map":
+        yield (0, 256, 0, 0)
+        for v in (1, 2, 3):
+            for blk in (128, 256, 512):
+                for e in (1, 2, 4):
+                    yield (v, blk, e, 0)
+    elif sk_name in ("reduce", "mapreduce"):
+        for v in (0, 1, 2):
+            for blk in (128, 256, 512):
+                for e in (1, 2, 4, 8):
+                    yield (v, blk, e, 0)
+    elif sk_name == "scan":
+        for v in (0, 1, 2):
+            for e in (2, 4, 8):
+                yield (v, 256, e, 0)
+    elif sk_name == "mapoverlap2d":
+        yield (0, 256, 0, 0)
+        yield (1, 256, 0, 0)
+        yield (2, 256, 0, 0)
+        for t in (16, 32, 64, 128):
+            yield (3, 128, 0, t)
+    elif sk_name == "mapoverlap1d":
+        yield (0, 256, 0, 0)
+        yield (1, 256, 8, 0)
+    elif sk_name == "maparray":
+        for v in (0, 1, 2):
+            yield (v, 256, 0, 0)
+    elif sk_name == "batched":
+        for v in (0, 1):
+            for e in (2, 4, 8):
+                yield (v, 256, e, 0)
+
+
+class Instance:
+    """One skeleton instance (skeleton + user function + dtype) with buffers
+    for its largest size; call(n) runs it on the first n elements."""
+
+    def __init__(self, name, sk_name, fn_key, dtype, radius, nmax, make, nbytes, sizes):
+        self.name, self.sk_name, self.fn_key, self.dtype, self.radius = name, sk_name, fn_key, dtype, radius
+        self.nmax, self.make, self.nbytes, self.sizes = nmax, make, nbytes, sizes
+
+
+def instances(nmax_log2: int):
+    nmax = 1 << nmax_log2
+    sizes = [1 << (2 * k) for k in range(5, nmax_log2 // 2 + 1)]
+    dev = torch.device("cuda")
+    out = []
+
+    def vec(n, lo=-1.0, hi=1.0):
+        return (torch.rand(n, device=dev) * (hi - lo) + lo).contiguous()
+
+    def mk_map(fn, nin):
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                bufs["x"], bufs["y"], bufs["o"] = vec(nmax), vec(nmax), vec(nmax)
+            ins = [Container.from_tensor(bufs["x"][:n])] + ([Container.from_tensor(bufs["y"][:n])] if nin == 2 else [])
+            o = Container.from_tensor(bufs["o"][:n])
+            return lambda: skel_map(fn, ins, o, [2.5] if fn == "axpy" else [])
+        return make
+
+    out.append(Instance("map axpy f32", "map", FN["axpy"], F32, 0, nmax, mk_map("axpy", 2), lambda n: 12 * n, sizes))
+    out.append(Instance("map tanh f32", "map", FN["tanh"], F32, 0, nmax, mk_map("tanh", 1), lambda n: 8 * n, sizes))
+
+    def mk_red(op, dt):
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                bufs["x"] = vec(nmax) if dt == F32 else torch.randint(0, 101, (nmax,), device=dev, dtype=torch.int32)
+                bufs["r"] = torch.zeros(1, device=dev, dtype=bufs["x"].dtype)
+            x, r = Container.from_tensor(bufs["x"][:n]), Container.from_tensor(bufs["r"])
+            return lambda: skel_reduce(op, x, r, host=False)
+        return make
+
+    for op in ("add", "max"):
+        for dt, dn in ((F32, "f32"), (I32, "i32")):
+            out.append(Instance(f"reduce {op} {dn}", "reduce", FN[op], dt, 0, nmax, mk_red(op, dt), lambda n: 4 * n, sizes))
+
+    def mk_mr(fn):
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                bufs["x"], bufs["y"], bufs["r"] = vec(nmax), vec(nmax), torch.zeros(1, device=dev)
+            ins = [Container.from_tensor(bufs["x"][:n])] + ([Container.from_tensor(bufs["y"][:n])] if fn == "mul" else [])
+            r = Container.from_tensor(bufs["r"])
+            return lambda: skel_mapreduce(fn, "add", ins, r, host=False)
+        return make
+
+    out.append(Instance("mapreduce dot f32", "mapreduce", FN["mul"], F32, 0, nmax, mk_mr("mul"), lambda n: 8 * n, sizes))
+    out.append(Instance("mapreduce sumsq f32", "mapreduce", FN["sq"], F32, 0, nmax, mk_mr("sq"), lambda n: 4 * n, sizes))
+
+    def mk_scan(dt, incl):
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                if dt == F32:
+                    bufs["x"], bufs["o"] = vec(nmax), vec(nmax)
+                else:
+                    bufs["x"] = torch.randint(0, 101, (nmax,), device=dev, dtype=torch.int32)
+                    bufs["o"] = torch.empty(nmax, device=dev, dtype=torch.int32)
+            x, o = Container.from_tensor(bufs["x"][:n]), Container.from_tensor(bufs["o"][:n])
+            return lambda: skel_scan("add", incl, x, o)
+        return make
+
+    for dt, dn in ((I32, "i32"), (F32, "f32")):
+        for incl in (True, False):
+            out.append(Instance(f"scan {'incl' if incl else 'excl'} {dn}", "scan", 1 if incl else 0, dt, 0, nmax,
+                                mk_scan(dt, incl), lambda n: 8 * n, sizes))
+
+    def mk_st2(fn):
+        bufs = {}
+
+        def make(n):
+            side = int(round(n ** 0.5))
+            if "x" not in bufs:
+                bufs["x"], bufs["o"] = vec(nmax, 0.0, 1.0), vec(nmax)
+            x = Container.from_tensor(bufs["x"][:side * side].view(side, side))
+            o = Container.from_tensor(bufs["o"][:side * side].view(side, side))
+            return lambda: skel_mapoverlap(fn, 1, None, "clamp", x, o)
+        return make
+
+    for fn in ("stencil9", "stencil5"):
+        out.append(Instance(f"mapoverlap2d {fn} clamp", "mapoverlap2d", FN[fn], F32, 1, nmax, mk_st2(fn),
+                            lambda n: 8 * n, sizes))
+
+    def mk_st1(r):
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                bufs["x"], bufs["o"] = vec(nmax), vec(nmax)
+            x, o = Container.from_tensor(bufs["x"][:n]), Container.from_tensor(bufs["o"][:n])
+            return lambda: skel_mapoverlap("stencil1d", r, None, "clamp", x, o)
+        return make
+
+    for r in (1, 4, 8, 16):
+        out.append(Instance(f"mapoverlap1d r={r} clamp", "mapoverlap1d", FN["stencil1d"], F32, r, nmax, mk_st1(r),
+                            lambda n: 8 * n, sizes))
+
+    def mk_rowdot():
+        bufs = {}
+
+        def make(m):   # key = row length m; rows so that the matrix holds min(nmax, 64 m) elements... at most nmax
+            rows = max(1, min(nmax // m, 1 << 14))
+            if "M" not in bufs:
+                bufs["M"], bufs["A"], bufs["o"] = vec(nmax), vec(nmax), vec(1 << 20)
+            A = Container.from_tensor(bufs["A"][:m])
+            M = Container.from_tensor(bufs["M"][:rows * m].view(rows, m))
+            o = Container.from_tensor(bufs["o"][:rows])
+            make.rows = rows
+            return lambda: skel_maparray("rowdot", A, M, o)
+        return make
+
+    rd = mk_rowdot()
+    out.append(Instance("maparray rowdot f32", "maparray", FN["rowdot"], F32, 0, nmax, rd,
+                        lambda m: 4 * m * max(1, min(nmax // m, 1 << 14)), sizes))
+
+    def mk_gather():
+        bufs = {}
+
+        def make(n):
+            if "i" not in bufs:
+                bufs["A"] = vec(1 << 20)
+                bufs["i"] = torch.randint(0, 1 << 20, (nmax,), device=dev, dtype=torch.int32)
+                bufs["o"] = vec(nmax)
+            A, i, o = (Container.from_tensor(bufs["A"]), Container.from_tensor(bufs["i"][:n]),
+                       Container.from_tensor(bufs["o"][:n]))
+            return lambda: skel_maparray("gather", A, i, o)
+        return make
+
+    out.append(Instance("maparray gather f32", "maparray", FN["gather"], F32, 0, nmax, mk_gather(), lambda n: 8 * n, sizes))
+    return out
+
+
+def batched_instance():
+    """The batched workload: 4096 log-uniform instances in [64, 2^20] (one
+    bucket; smaller and larger totals extrapolate from it)."""
+    import synthetic as syn
+    lens = syn.loguniform_lengths(syn.SEED_BATCH_LEN, 4096)
+    off = syn.csr_offsets(lens)
+    total = int(off[-1])
+    dev = torch.device("cuda")
+    v = torch.rand(total, device=dev) * 2 - 1
+    o = torch.from_numpy(off).to(dev)
+    res = torch.empty(4096, device=dev)
+    sc = torch.empty(total, device=dev)
+    cv, co, cr, cs = (Container.from_tensor(t) for t in (v, o, res, sc))
+    return total, (lambda: skel_batched(cv, co, cr, cs, True)), 8 * total
+
+
+def bucket(n: int) -> int:
+    return min(15, (int(n).bit_length() - 1) // 2)
+
+
+def tune(args):
+    timer = Timer()
+    lines = ["# execution-plan table of libskel.so, written by paper_1405_2915_gb300.tune on "
+             + torch.cuda.get_device_name(),
+             "# skeleton fn dtype bucket radius residency variant block ept tile"]
+    report = ["| skeleton instance | n | default GB/s | tuned GB/s | speedup | chosen |", "|---|---|---|---|---|---|"]
+    chosen_all = []
+    skel_load_dispatch_table(None)
+    for inst in instances(args.nmax_log2):
+        if args.only and not any(s in inst.name for s in args.only):
+            continue
+        sk_id = SK[inst.sk_name]
+        for n in inst.sizes:
+            fn = inst.make(n)
+            nb = inst.nbytes(n)
+            skel_force_variant(sk_id, -1)
+            t_def = timer.time(fn, nb, args.reps)
+            best, t_best = None, t_def
+            for cand in candidates(inst.sk_name):
+                skel_force_variant(sk_id, *cand)
+                try:
+                    t = timer.time(fn, nb, args.reps)
+                except SkelError:
+                    continue
+                finally:
+                    skel_force_variant(sk_id, -1)
+                if t < t_best:
+                    best, t_best = cand, t
+            if best is not None and t_best < t_def * (1.0 - args.margin):
+                lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 "
+                             f"{best[0]} {best[1]} {best[2]} {best[3]}")
+                chosen = best
+                t_tuned = t_best
+            else:
+                chosen, t_tuned = "default", t_def
+            chosen_all.append((inst.name, n, chosen))
+            report.append(f"| {inst.name} | {n} | {nb / t_def / 1e6:.1f} | {nb / t_tuned / 1e6:.1f} | "
+                          f"{t_def / t_tuned:.3f} | {chosen} |")
+            print(report[-1], flush=True)
+    if not args.only or "batched" in args.only:
+        total, fn, nb = batched_instance()
+        sk_id = SK["batched"]
+        t_def = timer.time(fn, nb, args.reps)
+        best, t_best = None, t_def
+        for cand in candidates("batched"):
+            skel_force_variant(sk_id, *cand)
+            try:
+                t = timer.time(fn, nb, args.reps)
+            except SkelError:
+                continue
+            finally:
+                skel_force_variant(sk_id, -1)
+            if t < t_best:
+                best, t_best = cand, t
+        if best is not None and t_best < t_def * (1.0 - args.margin):
+            lines.append(f"{sk_id} 0 {F32} {bucket(total)} 0 0 {best[0]} {best[1]} {best[2]} {best[3]}")
+        report.append(f"| batched sumsq+scan f32 | {total} | {nb / t_def / 1e6:.1f} | {nb / t_best / 1e6:.1f} | "
+                      f"{t_def / t_best:.3f} | {best if best and t_best < t_def * (1 - args.margin) else 'default'} |")
+        print(report[-1], flush=True)
+    with open(args.out, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    return report
+
+
+def validate(args):
+    """Tuned table vs defaults at sizes between the buckets (n = 2 * 4^k)."""
+    timer = Timer()
+    rows = ["| skeleton instance | n (between buckets) | default GB/s | table GB/s | table / default |",
+            "|---|---|---|---|---|"]
+    worst = 10.0
+    for inst in instances(args.nmax_log2):
+        if args.only and not any(s in inst.name for s in args.only):
+            continue
+        for n in [2 * s for s in inst.sizes if 2 * s <= inst.nmax]:
+            if inst.sk_name == "mapoverlap2d":
+                continue   # square grids only: between-bucket sizes are not squares
+            fn = inst.make(n)
+            nb = inst.nbytes(n)
+            skel_load_dispatch_table(None)
+            t_def = timer.time(fn, nb, args.reps)
+            skel_load_dispatch_table(args.out)
+            t_tab = timer.time(fn, nb, args.reps)
+            worst = min(worst, t_def / t_tab)
+            rows.append(f"| {inst.name} | {n} | {nb / t_def / 1e6:.1f} | {nb / t_tab / 1e6:.1f} | {t_def / t_tab:.3f} |")
+            print(rows[-1], flush=True)
+    rows.append(f"\nworst table/default speed ratio between buckets: {worst:.3f}")
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--out", default=os.path.join(os.path.dirname(os.path.abspath(__file__)), "dispatch_gb300.tbl"))
+    ap.add_argument("--report", default=None)
+    ap.add_argument("--reps", type=int, default=15)
+    ap.add_argument("--margin", type=float, default=0.03)
+    ap.add_argument("--nmax-log2", type=int, default=28)
+    ap.add_argument("--only", nargs="*", default=None)
+    ap.add_argument("--no-validate", action="store_true")
+    args = ap.parse_args()
+    t0 = time.time()
+    report = tune(args)
+    val = [] if args.no_validate else validate(args)
+    if args.report:
+        with open(args.report, "w") as f:
+            f.write(f"# Tuned vs default variants on {torch.cuda.get_device_name()}\n\n")
+            f.write("Command: `python -m paper_1405_2915_gb300.tune --report " + args.report + "`\n\n")
+            f.write("Device time per call, median of %d runs (CUDA events), L2 flushed before each run when the "
+                    "operands fit in L2.  GB/s = algorithmic bytes / time.\n\n" % args.reps)
+            f.write("\n".join(report) + "\n\n## Sizes between the tuned buckets\n\n" + "\n".join(val) + "\n")
+    print(f"tuned in {time.time() - t0:.0f} s -> {args.out}", file=sys.stderr)
+
+
+if __name__ == "__main__":
+    main()

@@ -24,7 +24,7 @@ def sk():
 
 def header_functions():
     text = open(os.path.join(ROOT, "include", "skel.h")).read()
-    return set(re.findall(r"^(?:int|const char \*)\s*\*?(skel_\w+)\(", text, re.M))
+    return set(re.findall(r"^(?:int|int64_t|const char \*)\s*\*?(skel_\w+)\(", text, re.M))
 
 
 def test_header_binding_and_exports_agree(sk):

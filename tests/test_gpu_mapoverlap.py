@@ -30,13 +30,19 @@ def test_mapoverlap2d(variant, tile, shape, kind, boundary):
     dout = dev_empty(shape, torch.float32)
     fn = "stencil5" if kind == "5pt" else "stencil9"
     with forced("mapoverlap2d", variant, 0, 0, tile):
+        if variant != 0 and shape[1] % 4:
+            # selectability constraint of the tiled variants; a forced call does not fall back
+            with pytest.raises(sk.SkelError) as e:
+                sk.skel_mapoverlap(fn, 1, None, boundary, wrap(dev_tensor(x)), wrap(dout))
+            assert e.value.code == -4
+            return
         sk.skel_mapoverlap(fn, 1, None, boundary, wrap(dev_tensor(x)), wrap(dout))
     ref = oracle.mapoverlap2d_f32(x, 1, weights(kind), boundary)
     assert_elem_close(to_np(dout), ref, f"{kind} {boundary} {shape} v{variant}")
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (5, 4), (64, 68), (257, 516)])
+@pytest.mark.parametrize("shape", [(1, 4), (2, 8), (5, 4), (64, 68), (257, 516), (3, 1028)])
 @pytest.mark.parametrize("boundary", BOUNDS)
 def test_mapoverlap2d_general_weights_and_adjoint(variant, shape, boundary):
     import torch
@@ -44,7 +50,7 @@ def test_mapoverlap2d_general_weights_and_adjoint(variant, shape, boundary):
     w = syn.uniform_f32(77, 9, -1.0, 1.0).reshape(3, 3)
     x = syn.uniform_f32(78, shape[0] * shape[1]).reshape(shape)
     dout = dev_empty(shape, torch.float32)
-    with forced("mapoverlap2d", variant):
+    with forced("mapoverlap2d", variant, 0, 0, 32 if variant == 3 else 0):
         sk.skel_mapoverlap("stencil9", 1, w, boundary, wrap(dev_tensor(x)), wrap(dout))
         assert_elem_close(to_np(dout), oracle.mapoverlap2d_f32(x, 1, w, boundary), "forward", atol=3e-6)
         sk.skel_mapoverlap_bwd("stencil9", 1, w, boundary, wrap(dev_tensor(x)), wrap(dout))
