@@ -380,9 +380,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default=None,
+                    help="profiling: comma-separated call names; times only those calls (no default-variant, "
+                         "e2e or CPU legs)")
+    ap.add_argument("--n-log2", type=int, default=28, help="profiling: elements per skeleton (even, >= 16)")
+    ap.add_argument("--batched-instances", type=int, default=4096, help="profiling: batched instance count")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    global N, SIDE, BATCH_B
+    if args.n_log2 != 28:
+        if args.n_log2 % 2 or args.n_log2 < 16:
+            ap.error("--n-log2 must be even and >= 16")
+        N, SIDE = 1 << args.n_log2, 1 << (args.n_log2 // 2)
+    BATCH_B = args.batched_instances
     if args.impl == "reference":
         run_reference(args)
         return
@@ -404,6 +415,12 @@ def main():
         sk.skel_load_dispatch_table(TABLE)
     wl = Workload(sk, torch, rank)
     calls = wl.calls()
+    if args.only:
+        keep = set(args.only.split(","))
+        calls = [c for c in calls if c[0] in keep]
+        if not calls:
+            ap.error("--only matched no call")
+        args.no_e2e = args.no_cpu = True
     stream = torch.cuda.current_stream()
     step_bytes = sum(b for _, b, _ in calls)
 
@@ -433,13 +450,16 @@ def main():
     value = world * step_bytes / (ms_step * 1e-3) / 1e9
 
     # the fixed default variants (empty table), same steps
-    sk.skel_load_dispatch_table(None)
-    run_steps(torch, calls, 3, stream, per_call=False)
-    barrier()
-    def_ms, per_def = run_steps(torch, calls, args.steps, stream)
-    barrier()
-    if tuned:
-        sk.skel_load_dispatch_table(TABLE)
+    if args.only:
+        def_ms, per_def = total_ms, per
+    else:
+        sk.skel_load_dispatch_table(None)
+        run_steps(torch, calls, 3, stream, per_call=False)
+        barrier()
+        def_ms, per_def = run_steps(torch, calls, args.steps, stream)
+        barrier()
+        if tuned:
+            sk.skel_load_dispatch_table(TABLE)
 
     hbm, peak_kind = peaks()
     per_sk = {}

@@ -729,9 +729,9 @@ int skel_batched(skel_fn map_fn, skel_fn red_op, skel_fn scan_op, int inclusive,
         Context ctx{SKEL_SK_BATCHED, 0, SKEL_F32, b.total, 0, res};
         return run_with_fallback(SKEL_SK_BATCHED, ctx, [&](const Choice &c) {
             Scratch scr{};
-            int r2 = get_scratch(s, batched_data_bytes(b, c), batched_flag_count(b, c), &scr);
+            int r2 = get_scratch(s, batched_data_bytes(b, c), batched_word_count(b, c), &scr);
             if (r2) return r2;
-            return launch_batched(b, c, scr.ctl, scr.flags, scr.data, scr.epoch, s);
+            return launch_batched(b, c, scr.ctl, scr.words, scr.data, scr.epoch, s);
         }, bat_def);
     });
 }
@@ -757,8 +757,8 @@ int skel_batched_plan_create(skel_fn map_fn, skel_fn red_op, skel_fn scan_op, in
         auto *p = new skel_plan_s();
         p->alloc = current_allocator();
         p->alloc_stream = s;
-        const size_t nflags = (batched_flag_count(b, c) + 63) & ~(size_t)63;
-        const size_t total = sizeof(Control) + nflags * 4 + batched_data_bytes(b, c);
+        const size_t nwords = (batched_word_count(b, c) + 31) & ~(size_t)31;
+        const size_t total = sizeof(Control) + nwords * 8 + batched_data_bytes(b, c);
         p->scratch = dev_alloc(p->alloc, total, s);
         if (!p->scratch) { delete p; return fail(SKEL_ERR_OOM, "plan scratch allocation failed"); }
         cudaError_t e = cudaMemsetAsync(p->scratch, 0, total, s);
@@ -767,17 +767,17 @@ int skel_batched_plan_create(skel_fn map_fn, skel_fn red_op, skel_fn scan_op, in
         cudaStream_t cap;
         SKEL_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         Control *ctl = static_cast<Control *>(p->scratch);
-        uint32_t *flags = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(p->scratch) + sizeof(Control));
-        unsigned char *data = reinterpret_cast<unsigned char *>(flags + nflags);
+        uint64_t *words = reinterpret_cast<uint64_t *>(static_cast<unsigned char *>(p->scratch) + sizeof(Control));
+        unsigned char *data = reinterpret_cast<unsigned char *>(words + nwords);
         // relaxed: the launcher queries occupancy (a host-side call) while capturing
         e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            // every replay starts from cleared look-back flags and abort word
+            // every replay starts from cleared look-back words and abort word
             // (the counters are reset by the kernels themselves; the error
-            // word stays sticky)
-            e = cudaMemsetAsync(flags, 0, nflags * 4, cap);
+            // word stays sticky), so all replays can use epoch 1
+            e = cudaMemsetAsync(words, 0, nwords * 8, cap);
             if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->abort, 0, sizeof(uint32_t), cap);
-            if (e == cudaSuccess) rc = launch_batched(b, c, ctl, flags, data, 1u, cap);
+            if (e == cudaSuccess) rc = launch_batched(b, c, ctl, words, data, 1u, cap);
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cap, &g);
             if (e == cudaSuccess) e = e2;

@@ -37,9 +37,10 @@ const DeviceInfo &device_info();  // of the current device
 
 // ------------------------------------------------------- scratch memory --
 // Layout of a scratch block: a 256-byte control block, a region of look-back
-// flag words, then the data region.  Kernels leave the control counters at
-// zero when they finish.  The flag region holds nothing but flag words
-// (epoch << 2 | status), so a stale word can only carry an older epoch.
+// descriptor words, then the data region.  Kernels leave the control counters
+// at zero when they finish.  The word region holds nothing but self-validating
+// look-back words tagged with a call's epoch (1..255), so a stale word can
+// only carry an older epoch; the region is cleared when the epoch wraps.
 struct Control {
     uint32_t ticket;     // tile ticket counter (single-pass scan, batched)
     uint32_t done;       // blocks finished (single-pass reduce)
@@ -55,18 +56,19 @@ constexpr uint32_t kErrInput = 2u;     // device-resident input failed validatio
 
 struct Scratch {
     Control *ctl;        // device address of the control block
-    uint32_t *flags;     // look-back flag words (flag_count requested)
+    uint64_t *words;     // look-back descriptor words (word_count requested)
     unsigned char *data; // device address of the data region (256-byte aligned)
     size_t data_bytes;
-    uint32_t epoch;      // tag of this call's look-back flags (never 0)
+    uint32_t epoch;      // tag of this call's look-back words, 1..255
 };
+constexpr uint32_t kMaxEpoch = 255;
 
 // Returns scratch for `stream` with at least `data_bytes` of data region and
-// `flag_count` flag words.  Scratch is cached per (device, stream) and reused
-// by later calls on the same stream (stream order serialises them).  A call
-// asking for flags gets a fresh epoch (the flags are cleared when the epoch
-// counter wraps or the flag region grows).
-int get_scratch(cudaStream_t stream, size_t data_bytes, size_t flag_count, Scratch *out);
+// `word_count` descriptor words.  Scratch is cached per (device, stream) and
+// reused by later calls on the same stream (stream order serialises them).
+// A call asking for words gets a fresh epoch (the words are cleared when the
+// epoch counter wraps or the region grows).
+int get_scratch(cudaStream_t stream, size_t data_bytes, size_t word_count, Scratch *out);
 
 // Control block of the scratch of `stream`, or nullptr if none was made.
 Control *scratch_control(cudaStream_t stream);
@@ -214,11 +216,12 @@ struct BatchedLaunch {
     float *scan_out;          // total (may be NULL)
 };
 // Scratch the batched launch needs for this call: data bytes and look-back
-// flag words (upper bounds from the total length and the instance count; the
-// plan allocates them itself, the direct call uses the stream's scratch).
+// descriptor words (upper bounds from the total length and the instance
+// count; the plan allocates them itself, the direct call uses the stream's
+// scratch).
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c);
-size_t batched_flag_count(const BatchedLaunch &b, const Choice &c);
-int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags,
+size_t batched_word_count(const BatchedLaunch &b, const Choice &c);
+int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words,
                    unsigned char *data, uint32_t epoch, cudaStream_t s);
 int batched_variant_count();
 const char *batched_variant_name(int v);

@@ -15,8 +15,10 @@
 //           scans them, sums their squares, and finds both prefixes with a
 //           look-back over the earlier tiles of its instance, carrying the
 //           pair in float64.  The last tile of an instance writes its sum.
-// Variants: 0 persistent (grid = SMs x resident blocks per SM),
-//           1 one_per_tile (grid = the tile bound; surplus blocks exit).
+// Variants: 0 persistent (grid = SMs x resident blocks per SM), look-back
+//             walked by warp 0;
+//           1 one_per_tile (grid = the tile bound; surplus blocks exit);
+//           2 persistent with the whole block walking the look-back.
 #include "scan_tile.cuh"
 
 namespace skel {
@@ -29,8 +31,6 @@ struct Layout {
     int64_t *tile_start;   // B + 1
     int32_t *tile_inst;    // max_tiles
     int64_t *total_tiles;  // 1
-    Pair *aggs;            // max_tiles
-    Pair *incls;           // max_tiles
 };
 
 size_t r256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -47,16 +47,14 @@ Layout layout(unsigned char *data, const BatchedLaunch &b, int tile)
     size_t off = 0;
     L.tile_start = reinterpret_cast<int64_t *>(data + off); off += r256((b.B + 1) * 8);
     L.tile_inst = reinterpret_cast<int32_t *>(data + off);  off += r256(mt * 4);
-    L.total_tiles = reinterpret_cast<int64_t *>(data + off); off += 256;
-    L.aggs = reinterpret_cast<Pair *>(data + off);           off += r256(mt * sizeof(Pair));
-    L.incls = reinterpret_cast<Pair *>(data + off);
+    L.total_tiles = reinterpret_cast<int64_t *>(data + off);
     return L;
 }
 
 size_t layout_bytes(const BatchedLaunch &b, int tile)
 {
     const int64_t mt = max_tiles(b, tile);
-    return r256((b.B + 1) * 8) + r256(mt * 4) + 256 + 2 * r256(mt * sizeof(Pair));
+    return r256((b.B + 1) * 8) + r256(mt * 4) + 256;
 }
 
 __device__ __forceinline__ int64_t ntiles_of(int64_t lo, int64_t hi, int tile)
@@ -104,21 +102,24 @@ batched_prep(const int64_t *__restrict__ off, int64_t B, int64_t total, int tile
 #pragma unroll
         for (int i = 0; i < IPT; ++i) {
             const int64_t b = c0 + (int64_t)threadIdx.x * IPT + i;
-            if (b < B) {
-                L.tile_start[b] = run;
-                for (int64_t k = 0; k < cnt[i] && run + k < max_t; ++k) L.tile_inst[run + k] = (int32_t)b;
-            }
+            if (b < B) L.tile_start[b] = run;
             run += cnt[i];
         }
         carry += smem[32];
         __syncthreads();
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
         L.tile_start[B] = carry;
         const bool ok = !bad && carry <= max_t;
         *L.total_tiles = ok ? carry : 0;
         if (!ok) atomicOr(&ctl->error, kErrInput);
+    }
+    __syncthreads();   // tile_start is complete (global writes of this block)
+    // tile -> instance map: warp w fills the tiles of instances w, w+32, ...,
+    // its lanes writing consecutive entries
+    for (int64_t b = w; b < B; b += 32) {
+        const int64_t s0 = L.tile_start[b], s1 = L.tile_start[b + 1];
+        for (int64_t k = s0 + lane; k < s1 && k < max_t; k += 32) L.tile_inst[k] = (int32_t)b;
     }
 }
 
@@ -160,18 +161,22 @@ __device__ __forceinline__ void store_masked(float *__restrict__ out, int64_t fb
     }
 }
 
-template <bool SCAN, bool RED, bool INCL, int V>
+// BLK: the whole block walks the look-back (variant 2) or warp 0 alone
+// (variants 0, 1).  words: 2 * max_t aggregate words, then 2 * max_t prefix words.
+template <bool SCAN, bool RED, bool INCL, int V, bool BLK>
 __global__ void __launch_bounds__(kBlock)
 batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ results,
-             float *__restrict__ scan_out, Layout L, uint32_t *flags, Control *ctl, uint32_t epoch, uint64_t limit_ns)
+             float *__restrict__ scan_out, Layout L, uint64_t *words, int64_t max_t, Control *ctl, uint32_t epoch,
+             uint64_t limit_ns)
 {
     constexpr int TILE = kBlock * 4 * V;
     __shared__ float smem[kBlock / 32 + 1];
     __shared__ float red_smem[32];
     __shared__ int64_t s_tile;
     __shared__ Pair s_prefix;
+    __shared__ dev::BlockLookbackSmem<Pair, kBlock> lbs;
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
-    dev::LookbackDesc<Pair> d{flags, L.aggs, L.incls};
+    const dev::LookbackDesc d{words, words + 2 * max_t};
     while (true) {
         if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctl->queue, 1u);
         __syncthreads();
@@ -194,17 +199,23 @@ batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, 
         }
         float sagg = 0.f;
         if (SCAN) sagg = dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
-        if (threadIdx.x < 32) {
-            const Pair agg((double)sagg, (double)q);
-            Pair p = first == last ? Pair(0.0) : dev::lookback<Pair>(t, first, agg, d, epoch, ctl, limit_ns, true);
-            if (threadIdx.x == 0) {
-                s_prefix = p;
-                if (RED && t == last) results[b] = (float)(p.q + agg.q);
+        const Pair agg((double)sagg, (double)q);
+        Pair p(0.0);
+        if (first != last) {   // block-uniform
+            if (BLK) {
+                p = dev::block_lookback<Pair, kBlock>(t, first, agg, d, epoch, ctl, limit_ns, true, lbs);
+            } else {
+                if (threadIdx.x < 32) {
+                    const Pair w = dev::lookback<Pair>(t, first, agg, d, epoch, ctl, limit_ns, true);
+                    if (threadIdx.x == 0) s_prefix = w;
+                }
+                __syncthreads();
+                p = s_prefix;
             }
         }
-        __syncthreads();
+        if (RED && t == last && threadIdx.x == 0) results[b] = (float)(p.q + agg.q);
         if (SCAN) {
-            dev::tile_add_prefix<float, V>(v, (float)s_prefix.s);
+            dev::tile_add_prefix<float, V>(v, (float)p.s);
             store_masked<V>(scan_out, fbase, lo, hi, v);
         }
         __syncthreads();   // s_tile / s_prefix are rewritten by the next iteration
@@ -219,10 +230,10 @@ batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, 
 }
 
 template <bool SCAN, bool RED, bool INCL, int V>
-int run_main(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags, const Layout &L,
+int run_main(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, const Layout &L,
              uint32_t epoch, int64_t max_t, cudaStream_t s)
 {
-    auto kern = batched_main<SCAN, RED, INCL, V>;
+    auto kern = c.variant == 2 ? batched_main<SCAN, RED, INCL, V, true> : batched_main<SCAN, RED, INCL, V, false>;
     int64_t grid;
     if (c.variant == 1) {
         grid = max_t;
@@ -236,14 +247,14 @@ int run_main(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *fl
     if (grid < 1) grid = 1;
     if (grid > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "batched: too many tiles");
     const DebugKnobs k = debug_knobs();
-    launch_kernel(kern, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.results, b.scan_out, L, flags, ctl, epoch,
-                                           k.wait_limit_ns);
+    launch_kernel(kern, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.results, b.scan_out, L, words, max_t, ctl,
+                  epoch, k.wait_limit_ns);
     cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "batched launch");
 }
 
 template <int V>
-int run_v(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags, unsigned char *data,
+int run_v(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, unsigned char *data,
           uint32_t epoch, cudaStream_t s)
 {
     constexpr int TILE = kBlock * 4 * V;
@@ -254,41 +265,42 @@ int run_v(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prep launch");
     if (b.want_scan && b.want_reduce)
-        return b.inclusive ? run_main<true, true, true, V>(b, c, ctl, flags, L, epoch, mt, s)
-                           : run_main<true, true, false, V>(b, c, ctl, flags, L, epoch, mt, s);
+        return b.inclusive ? run_main<true, true, true, V>(b, c, ctl, words, L, epoch, mt, s)
+                           : run_main<true, true, false, V>(b, c, ctl, words, L, epoch, mt, s);
     if (b.want_scan)
-        return b.inclusive ? run_main<true, false, true, V>(b, c, ctl, flags, L, epoch, mt, s)
-                           : run_main<true, false, false, V>(b, c, ctl, flags, L, epoch, mt, s);
-    return run_main<false, true, true, V>(b, c, ctl, flags, L, epoch, mt, s);
+        return b.inclusive ? run_main<true, false, true, V>(b, c, ctl, words, L, epoch, mt, s)
+                           : run_main<true, false, false, V>(b, c, ctl, words, L, epoch, mt, s);
+    return run_main<false, true, true, V>(b, c, ctl, words, L, epoch, mt, s);
 }
 
 int tile_of(const Choice &c) { return kBlock * 4 * (c.ept > 0 ? c.ept : 4); }
 
 }  // namespace
 
-int batched_variant_count() { return 2; }
+int batched_variant_count() { return 3; }
 const char *batched_variant_name(int v)
 {
-    static const char *names[] = {"persistent", "one_per_tile"};
-    return v >= 0 && v < 2 ? names[v] : "?";
+    static const char *names[] = {"persistent", "one_per_tile", "persistent_block_lookback"};
+    return v >= 0 && v < 3 ? names[v] : "?";
 }
 Choice batched_default() { return Choice{0, 256, 4, 0}; }
 
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c) { return layout_bytes(b, tile_of(c)); }
-size_t batched_flag_count(const BatchedLaunch &b, const Choice &c) { return (size_t)max_tiles(b, tile_of(c)); }
+// aggregate and prefix of every tile, two words (scan carry, sum of squares) each
+size_t batched_word_count(const BatchedLaunch &b, const Choice &c) { return 4 * (size_t)max_tiles(b, tile_of(c)); }
 
-int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint32_t *flags, unsigned char *data,
+int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, unsigned char *data,
                    uint32_t epoch, cudaStream_t s)
 {
-    if (c.variant < 0 || c.variant > 1) return fail(SKEL_ERR_INVALID_ARG, "batched: unknown variant");
+    if (c.variant < 0 || c.variant > 2) return fail(SKEL_ERR_INVALID_ARG, "batched: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "batched: block must be 256");
     if (!aligned16(b.values) || (b.scan_out && !aligned16(b.scan_out)))
         return fail(SKEL_ERR_UNSUPPORTED, "batched: values and scan_out must be 16-byte aligned");
     if (b.B == 0) return SKEL_OK;
     switch (c.ept > 0 ? c.ept : 4) {
-    case 2: return run_v<2>(b, c, ctl, flags, data, epoch, s);
-    case 4: return run_v<4>(b, c, ctl, flags, data, epoch, s);
-    case 8: return run_v<8>(b, c, ctl, flags, data, epoch, s);
+    case 2: return run_v<2>(b, c, ctl, words, data, epoch, s);
+    case 4: return run_v<4>(b, c, ctl, words, data, epoch, s);
+    case 8: return run_v<8>(b, c, ctl, words, data, epoch, s);
     default: return fail(SKEL_ERR_INVALID_ARG, "batched: ept must be 2, 4 or 8");
     }
 }

@@ -67,11 +67,17 @@ rowdot_warp(const float *__restrict__ A, int64_t m, const float *__restrict__ M,
             const float4 *A4 = reinterpret_cast<const float4 *>(A);
             const int64_t mv = m / 4;
             int64_t k = lane;
-            for (; k + 32 < mv; k += 64) {   // two 16-byte loads in flight per lane
-                const float4 p = dev::ld_stream(r4 + k), q = dev::ld_stream(r4 + k + 32);
-                const float4 ap = __ldg(A4 + k), aq = __ldg(A4 + k + 32);
-                a0 = fmaf(ap.x, p.x, a0); a1 = fmaf(ap.y, p.y, a1); a2 = fmaf(ap.z, p.z, a2); a3 = fmaf(ap.w, p.w, a3);
-                a0 = fmaf(aq.x, q.x, a0); a1 = fmaf(aq.y, q.y, a1); a2 = fmaf(aq.z, q.z, a2); a3 = fmaf(aq.w, q.w, a3);
+            for (; k + 96 < mv; k += 128) {   // four 16-byte row loads in flight per lane
+                float4 p[4], ap[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) p[u] = dev::ld_stream(r4 + k + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) ap[u] = __ldg(A4 + k + 32 * u);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a0 = fmaf(ap[u].x, p[u].x, a0); a1 = fmaf(ap[u].y, p[u].y, a1);
+                    a2 = fmaf(ap[u].z, p[u].z, a2); a3 = fmaf(ap[u].w, p[u].w, a3);
+                }
             }
             for (; k < mv; k += 32) {
                 const float4 p = dev::ld_stream(r4 + k);

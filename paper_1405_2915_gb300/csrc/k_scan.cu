@@ -14,6 +14,11 @@
 //                       predecessors.  8 bytes per element, the minimum.
 //   2 one_block         one block walks the tiles in order with a carried
 //                       prefix (small n: no inter-block traffic at all).
+//   3 lookback_block    variant 1 with the whole block walking the look-back,
+//                       one predecessor per thread (256 per round): with many
+//                       tiles in flight the nearest published prefix lies far
+//                       back, and warp 0 alone needs many rounds while the
+//                       other warps wait at the barrier.
 // ept selects V, the 16-byte groups per thread (tile = 256 threads x 4V).
 // float32: element arithmetic is float32; the prefix carried from tile to
 // tile is float64 (one add per tile), rounded to float32 once per tile.
@@ -51,10 +56,12 @@ __device__ __forceinline__ TileMap tile_map(const SegGeom &g, int64_t tile, int6
     return m;
 }
 
-template <class T, bool INCL, int V>
+// BLK: the whole block walks the look-back (variant 3) instead of warp 0
+// alone (variant 1).
+template <class T, bool INCL, int V, bool BLK>
 __global__ void __launch_bounds__(kBlock)
 scan_lookback(const T *__restrict__ in, T *__restrict__ out, SegGeom g,
-              LookbackDesc<typename ScanTypes<T>::CT> d, Control *ctl, uint32_t epoch,
+              LookbackDesc d, Control *ctl, uint32_t epoch,
               int64_t skip_tile, uint64_t limit_ns)
 {
     using CT = typename ScanTypes<T>::CT;
@@ -62,6 +69,7 @@ scan_lookback(const T *__restrict__ in, T *__restrict__ out, SegGeom g,
     __shared__ T smem[kBlock / 32 + 1];
     __shared__ int64_t s_tile;
     __shared__ CT s_prefix;
+    __shared__ dev::BlockLookbackSmem<CT, kBlock> lbs;
     if (threadIdx.x == 0) {
         const uint32_t t = atomicAdd(&ctl->ticket, 1u);
         if ((int64_t)t == g.ntiles - 1) ctl->ticket = 0u;   // the last ticket: every CTA has drawn
@@ -74,12 +82,18 @@ scan_lookback(const T *__restrict__ in, T *__restrict__ out, SegGeom g,
     T v[V][4];
     dev::tile_load<T, kBlock, V>(in, m, v);
     const T agg = dev::tile_scan_local<T, INCL, kBlock, V>(v, smem);
-    if (threadIdx.x < 32) {
-        CT p = dev::lookback<CT>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, tile != skip_tile);
-        if (threadIdx.x == 0) s_prefix = p;
+    CT p;
+    if (BLK) {
+        p = dev::block_lookback<CT, kBlock>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, tile != skip_tile, lbs);
+    } else {
+        if (threadIdx.x < 32) {
+            CT q = dev::lookback<CT>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, tile != skip_tile);
+            if (threadIdx.x == 0) s_prefix = q;
+        }
+        __syncthreads();
+        p = s_prefix;
     }
-    __syncthreads();
-    dev::tile_add_prefix<T, V>(v, dev::to_elem<T>(s_prefix));
+    dev::tile_add_prefix<T, V>(v, dev::to_elem<T>(p));
     dev::tile_store<T, kBlock, V>(out, m, v);
 }
 
@@ -211,16 +225,16 @@ int run_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
         launch_kernel(scan_tile_apply<T, INCL, V>, (unsigned)g.ntiles, kBlock, 0, s, in, out, g, sums);
     } else {
         Scratch scr{};
-        const size_t vb = ((size_t)g.ntiles * sizeof(CT) + 255) & ~(size_t)255;
-        int rc = get_scratch(s, 2 * vb, (size_t)g.ntiles, &scr);
+        int rc = get_scratch(s, 0, 2 * (size_t)g.ntiles, &scr);   // one aggregate + one prefix word per tile
         if (rc) return rc;
-        LookbackDesc<CT> d;
-        d.flags = scr.flags;
-        d.aggs = reinterpret_cast<CT *>(scr.data);
-        d.incls = reinterpret_cast<CT *>(scr.data + vb);
+        LookbackDesc d{scr.words, scr.words + g.ntiles};
         const DebugKnobs k = debug_knobs();
-        launch_kernel(scan_lookback<T, INCL, V>, (unsigned)g.ntiles, kBlock, 0, s, 
-            in, out, g, d, scr.ctl, scr.epoch, k.scan_skip_publish_tile, k.wait_limit_ns);
+        if (c.variant == 3)
+            launch_kernel(scan_lookback<T, INCL, V, true>, (unsigned)g.ntiles, kBlock, 0, s,
+                          in, out, g, d, scr.ctl, scr.epoch, k.scan_skip_publish_tile, k.wait_limit_ns);
+        else
+            launch_kernel(scan_lookback<T, INCL, V, false>, (unsigned)g.ntiles, kBlock, 0, s,
+                          in, out, g, d, scr.ctl, scr.epoch, k.scan_skip_publish_tile, k.wait_limit_ns);
     }
     cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan launch");
@@ -240,18 +254,18 @@ int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 
 }  // namespace
 
-int scan_variant_count() { return 3; }
+int scan_variant_count() { return 4; }
 const char *scan_variant_name(int v)
 {
-    static const char *names[] = {"reduce_then_scan", "lookback", "one_block"};
-    return v >= 0 && v < 3 ? names[v] : "?";
+    static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block"};
+    return v >= 0 && v < 4 ? names[v] : "?";
 }
 Choice scan_default() { return Choice{0, 256, 4, 0}; }
 
 int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (sc.n == 0) return SKEL_OK;
-    if (c.variant < 0 || c.variant > 2) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
+    if (c.variant < 0 || c.variant > 3) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "scan: block must be 256");
     if (sc.seg > 0 && sc.n % sc.seg) return fail(SKEL_ERR_SHAPE, "scan: n is not a multiple of the segment");
     if (sc.dtype == SKEL_F32)

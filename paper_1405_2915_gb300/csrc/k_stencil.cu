@@ -96,18 +96,22 @@ template <bool TAPS5>
 __device__ __forceinline__ void tile_compute(const float *s, float *__restrict__ out, int64_t tx0, int64_t ty0,
                                              int64_t rows, int64_t cols, const W9 &w)
 {
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // a warp is one row of 32 lanes
     const int64_t c = tx0 + 4 * tx;
-    if (c >= cols) return;
     float rr[6][6];   // rows 4ty-1 .. 4ty+4, columns 4tx-1 .. 4tx+4
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const float *row = s + (4 * ty + i) * kSW + 4 * tx + 4;   // staged row of output row 4ty+i-1
         const float4 q = *reinterpret_cast<const float4 *>(row);
-        rr[i][0] = row[-1];
+        // left / right neighbours from the adjacent lanes; the warp's two edge
+        // lanes read theirs from shared memory
+        const float l = __shfl_up_sync(0xffffffffu, q.w, 1);
+        const float r = __shfl_down_sync(0xffffffffu, q.x, 1);
+        rr[i][0] = tx == 0 ? row[-1] : l;
         rr[i][1] = q.x; rr[i][2] = q.y; rr[i][3] = q.z; rr[i][4] = q.w;
-        rr[i][5] = row[4];
+        rr[i][5] = tx == 31 ? row[4] : r;
     }
+    if (c >= cols) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int64_t r = ty0 + 4 * ty + i;
@@ -322,19 +326,29 @@ template <int R>
 __global__ void __launch_bounds__(256)
 st1_smem(const float *__restrict__ in, float *__restrict__ out, int64_t n, int b, W33 w)
 {
-    constexpr int SW = k1Tile + 2 * R + 4;   // + slack so the last window reads stay in bounds
+    constexpr int WV = (k1Per + 2 * R + 3) / 4;        // 16-byte reads per window
+    constexpr int SW = k1Tile + 4 * WV;                // window of the last thread stays in bounds
     __shared__ __align__(16) float s[SW];
     const int64_t t0 = (int64_t)blockIdx.x * k1Tile;
-    for (int j = threadIdx.x; j < k1Tile + 2 * R; j += 256) {
-        const int64_t src = bmap(t0 - R + j, n, b);
-        s[j] = src < 0 ? 0.f : __ldg(in + src);
+    if (t0 - R >= 0 && t0 + k1Tile + R <= n) {         // interior block: no boundary map
+        for (int j = threadIdx.x; j < k1Tile + 2 * R; j += 256) s[j] = __ldg(in + t0 - R + j);
+    } else {
+        for (int j = threadIdx.x; j < k1Tile + 2 * R; j += 256) {
+            const int64_t src = bmap(t0 - R + j, n, b);
+            s[j] = src < 0 ? 0.f : __ldg(in + src);
+        }
     }
     for (int j = k1Tile + 2 * R + threadIdx.x; j < SW; j += 256) s[j] = 0.f;
     __syncthreads();
+    // thread t owns outputs 8t .. 8t+7; its window s[8t .. 8t+8+2R) is read as
+    // 16-byte vectors (a 32-byte stride between threads: two-way bank sharing)
     const int base = threadIdx.x * k1Per;
-    float win[k1Per + 2 * R];
+    float win[4 * WV];
 #pragma unroll
-    for (int j = 0; j < k1Per + 2 * R; ++j) win[j] = s[base + j];
+    for (int j = 0; j < WV; ++j) {
+        const float4 q = *reinterpret_cast<const float4 *>(s + base + 4 * j);
+        win[4 * j] = q.x; win[4 * j + 1] = q.y; win[4 * j + 2] = q.z; win[4 * j + 3] = q.w;
+    }
     float o[k1Per];
 #pragma unroll
     for (int q = 0; q < k1Per; ++q) {

@@ -109,7 +109,7 @@ void dev_free(const Allocator &a, void *p, cudaStream_t stream)
 namespace {
 struct ScratchBlock {
     void *base = nullptr;
-    size_t flag_cap = 0;    // flag words
+    size_t word_cap = 0;    // 64-bit look-back words
     size_t data_cap = 0;    // bytes
     uint32_t epoch = 0;
     Allocator alloc{};
@@ -120,32 +120,32 @@ std::map<std::pair<int, cudaStream_t>, ScratchBlock> g_scratch;
 size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace
 
-int get_scratch(cudaStream_t stream, size_t data_bytes, size_t flag_count, Scratch *out)
+int get_scratch(cudaStream_t stream, size_t data_bytes, size_t word_count, Scratch *out)
 {
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_scr_mu);
     ScratchBlock &b = g_scratch[{dev, stream}];
-    const bool grow = !b.base || data_bytes > b.data_cap || flag_count > b.flag_cap;
+    const bool grow = !b.base || data_bytes > b.data_cap || word_count > b.word_cap;
     if (grow) {
-        size_t fc = std::max(flag_count, b.flag_cap);
+        size_t wc = std::max(word_count, b.word_cap);
         size_t dc = std::max(data_bytes, b.data_cap);
         // grow geometrically so that a size sweep does not reallocate each call
         if (b.base) {
-            fc = std::max(fc, b.flag_cap + b.flag_cap / 2);
+            wc = std::max(wc, b.word_cap + b.word_cap / 2);
             dc = std::max(dc, b.data_cap + b.data_cap / 2);
         }
-        fc = std::max<size_t>(round256(fc * 4) / 4, 64);
+        wc = std::max<size_t>(round256(wc * 8) / 8, 32);
         dc = std::max<size_t>(round256(dc), 256);
         if (b.base) dev_free(b.alloc, b.base, stream);
         b.alloc = current_allocator();
-        const size_t total = sizeof(Control) + fc * 4 + dc;
+        const size_t total = sizeof(Control) + wc * 8 + dc;
         b.base = dev_alloc(b.alloc, total, stream);
         if (!b.base) {
             b = ScratchBlock{};
             return fail(SKEL_ERR_OOM, "scratch allocation failed");
         }
-        b.flag_cap = fc;
+        b.word_cap = wc;
         b.data_cap = dc;
         b.epoch = 0;
         cudaError_t e = cudaMemsetAsync(b.base, 0, total, stream);
@@ -153,15 +153,16 @@ int get_scratch(cudaStream_t stream, size_t data_bytes, size_t flag_count, Scrat
     }
     unsigned char *base = static_cast<unsigned char *>(b.base);
     out->ctl = reinterpret_cast<Control *>(base);
-    out->flags = reinterpret_cast<uint32_t *>(base + sizeof(Control));
-    out->data = base + sizeof(Control) + b.flag_cap * 4;
+    out->words = reinterpret_cast<uint64_t *>(base + sizeof(Control));
+    out->data = base + sizeof(Control) + b.word_cap * 8;
     out->data_bytes = b.data_cap;
-    if (flag_count > 0) {
+    if (word_count > 0) {
         b.epoch += 1;
-        if (b.epoch >= (1u << 30)) {   // tag space exhausted: clear every flag, restart
+        if (b.epoch > kMaxEpoch) {   // tag space used up: clear every word and the abort tag, restart
             b.epoch = 1;
-            cudaError_t e = cudaMemsetAsync(out->flags, 0, b.flag_cap * 4, stream);
-            if (e != cudaSuccess) return fail_cuda(e, "flag clear");
+            cudaError_t e = cudaMemsetAsync(out->words, 0, b.word_cap * 8, stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(&out->ctl->abort, 0, sizeof(uint32_t), stream);
+            if (e != cudaSuccess) return fail_cuda(e, "look-back word clear");
         }
     }
     out->epoch = b.epoch == 0 ? 1 : b.epoch;

@@ -141,116 +141,7 @@ __device__ __forceinline__ void tile_add_prefix(T (&v)[V][4], T p)
         for (int j = 0; j < 4; ++j) v[k][j] = p + v[k][j];
 }
 
-// ------------------------------------------------------------ look-back ---
-// Flag word of a tile: (epoch << 2) | status; status 1 = aggregate
-// published, 2 = inclusive prefix published.  A flag whose epoch is not the
-// current call's is "not published yet".
-constexpr uint32_t kStAgg = 1u, kStIncl = 2u;
-
-template <class CT>
-struct LookbackDesc {
-    uint32_t *flags;
-    CT *aggs;
-    CT *incls;
-};
-
-template <class CT> __device__ __forceinline__ CT ld_cg(const CT *p) { return __ldcg(p); }
-template <class CT> __device__ __forceinline__ CT shfl_xor_ct(CT v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-
-// Two float64 running values carried together (batched instances: the
-// scan carry and the sum of squares).
-struct Pair {
-    double s, q;
-    Pair() = default;   // trivial, so a __shared__ Pair needs no initialisation
-    __device__ __forceinline__ Pair(double v) : s(v), q(v) {}
-    __device__ __forceinline__ Pair(double a, double b) : s(a), q(b) {}
-};
-__device__ __forceinline__ Pair operator+(const Pair &a, const Pair &b) { return Pair(a.s + b.s, a.q + b.q); }
-template <> __device__ __forceinline__ Pair ld_cg<Pair>(const Pair *p)
-{
-    const double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
-    return Pair(v.x, v.y);
-}
-template <> __device__ __forceinline__ Pair shfl_xor_ct<Pair>(Pair v, int o)
-{
-    return Pair(__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.q, o));
-}
-
-// Run by all 32 lanes of one warp.  Publishes this tile's aggregate, walks
-// back over the predecessors of the same segment (tiles >= first) in windows
-// of 32 until it meets a published inclusive prefix, publishes this tile's
-// inclusive prefix and returns the exclusive prefix (all lanes).  The wait is
-// bounded by limit_ns (global timer) and by the shared abort word; on expiry
-// it records kErrTimeout, sets abort to this call's epoch (so the other
-// waiters of the same call stop at once, and a later call is unaffected) and
-// counts unpublished tiles as 0.
-template <class CT>
-__device__ __forceinline__ CT lookback(int64_t tile, int64_t first, CT agg, LookbackDesc<CT> d,
-                                       uint32_t epoch, Control *ctl, uint64_t limit_ns,
-                                       bool publish)
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t tag = epoch << 2;
-    if (tile == first) {
-        if (publish && lane == 0) {
-            d.incls[tile] = agg;
-            st_release(d.flags + tile, tag | kStIncl);
-        }
-        return CT(0);
-    }
-    if (publish && lane == 0) {
-        d.aggs[tile] = agg;
-        st_release(d.flags + tile, tag | kStAgg);
-    }
-    CT excl = CT(0);
-    int64_t pred = tile - 1;
-    uint64_t t0 = 0;
-    bool gave_up = false;
-    while (true) {
-        const int64_t p = pred - lane;
-        const bool inseg = p >= first;
-        uint32_t status = 0;
-        unsigned incl_mask = 0;
-        while (true) {
-            if (inseg) {
-                const uint32_t f = ld_acquire(d.flags + p);
-                status = (f & ~3u) == tag ? (f & 3u) : 0u;
-            } else {
-                status = kStIncl;    // before the segment start: prefix 0
-            }
-            const unsigned ready_mask = __ballot_sync(0xffffffffu, status != 0);
-            incl_mask = __ballot_sync(0xffffffffu, status == kStIncl);
-            const unsigned need = incl_mask ? (((incl_mask & (0u - incl_mask)) << 1) - 1u) : 0xffffffffu;
-            if ((ready_mask & need) == need || gave_up) break;
-            if (t0 == 0) t0 = globaltimer();
-            bool expired = (globaltimer() - t0 > limit_ns) || ld_volatile(&ctl->abort) == epoch;
-            expired = __any_sync(0xffffffffu, expired);
-            if (expired) {
-                if (lane == 0) {
-                    atomicOr(&ctl->error, kErrTimeout);
-                    atomicExch(&ctl->abort, epoch);
-                }
-                gave_up = true;
-            }
-        }
-        const unsigned lim = incl_mask ? (((incl_mask & (0u - incl_mask)) << 1) - 1u) : 0xffffffffu;
-        CT val = CT(0);
-        if ((lim >> lane) & 1u) {
-            if (status == kStIncl) val = inseg ? ld_cg(d.incls + p) : CT(0);
-            else if (status == kStAgg) val = ld_cg(d.aggs + p);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) val = val + shfl_xor_ct(val, o);
-        excl = excl + val;
-        if (incl_mask) break;
-        pred -= 32;
-    }
-    if (publish && lane == 0) {
-        d.incls[tile] = excl + agg;
-        st_release(d.flags + tile, tag | kStIncl);
-    }
-    return excl;
-}
-
 }  // namespace dev
 }  // namespace skel
+
+#include "lookback.cuh"

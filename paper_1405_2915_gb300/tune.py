@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 
 class Timer:
     def __init__(self):
-        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.flush = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
         self.stream = torch.cuda.current_stream()
 
     def time(self, fn, nbytes: int, reps: int) -> float:
@@ -47,7 +47,9 @@ class Timer:
         ts = []
         for _ in range(reps):
             if flush:
-                self.flush.zero_()
+                # read (not write) a buffer larger than L2: L2 ends up full of
+                # clean lines, so no write-back of flush data is charged to fn
+                self.flush.sum()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(self.stream)
             fn()
@@ -77,7 +79,7 @@ def candidates(sk_name: str):
                 for e in (1, 2, 4, 8):
                     yield (v, blk, e, 0)
     elif sk_name == "scan":
-        for v in (0, 1, 2):
+        for v in (0, 1, 2, 3):
             for e in (2, 4, 8):
                 yield (v, 256, e, 0)
     elif sk_name == "mapoverlap2d":
@@ -93,7 +95,7 @@ def candidates(sk_name: str):
         for v in (0, 1, 2):
             yield (v, 256, 0, 0)
     elif sk_name == "batched":
-        for v in (0, 1):
+        for v in (0, 1, 2):
             for e in (2, 4, 8):
                 yield (v, 256, e, 0)
 

@@ -1,0 +1,56 @@
+"""Failure detection without a GPU fault: a scan tile that never publishes
+makes its successors' bounded look-back waits run out; the kernel records the
+status, every launch still finishes, the host reads the status, and the
+context stays usable."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as syn
+from helpers import dev_empty, dev_tensor, forced, skel, to_np, wrap
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("variant", [1, 3])   # warp-wide and block-wide look-back
+def test_lookback_wait_runs_out_and_is_reported(variant):
+    import torch
+    sk = skel()
+    n = 20 * 4096 + 5
+    x = syn.uniform_int(1, n, 0, 100)
+    out = dev_empty((n,), torch.int32)
+    sk.skel_check_device()
+    sk.skel_set_debug(2, 50_000)        # 50 ms wait limit
+    sk.skel_set_debug(1, 3)             # tile 3 never publishes
+    try:
+        with forced("scan", variant):
+            sk.skel_scan("add", True, wrap(dev_tensor(x)), wrap(out))
+        with pytest.raises(sk.SkelError) as e:
+            sk.skel_check_device()
+        assert e.value.code == -7
+    finally:
+        sk.skel_set_debug(1, -1)
+        sk.skel_set_debug(2, 2_000_000)
+    # the status was cleared and the context works
+    sk.skel_check_device()
+    with forced("scan", variant):
+        sk.skel_scan("add", True, wrap(dev_tensor(x)), wrap(out))
+    sk.skel_check_device()
+    assert np.array_equal(to_np(out), oracle.scan_i32(x, True).astype(np.int32))
+
+
+def test_errors_are_reported_not_raised_across_the_abi():
+    import torch
+    sk = skel()
+    a = wrap(torch.zeros(10, device="cuda"))
+    b = wrap(torch.zeros(11, device="cuda"))
+    with pytest.raises(sk.SkelError) as e:
+        sk.skel_map("add", [a, b], a)
+    assert e.value.code == -2
+    with pytest.raises(sk.SkelError) as e:
+        sk.skel_scan("max", True, a, wrap(torch.zeros(10, device="cuda")))
+    assert e.value.code == -4
+    i = wrap(torch.zeros(10, dtype=torch.int64, device="cuda"))
+    with pytest.raises(sk.SkelError) as e:
+        sk.skel_reduce("add", i)
+    assert e.value.code == -3

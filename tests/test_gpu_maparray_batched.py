@@ -59,7 +59,7 @@ def check_batched(v, off, res, scan, inclusive):
         assert_prefix_close(scan, ref, ab, "batched scan")
 
 
-@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8)])
+@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8), (2, 4), (1, 8)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_batched_small_mixed(variant, ept, inclusive):
     """Empty, tiny, unaligned and multi-tile instances mixed."""

@@ -11,7 +11,7 @@ from helpers import assert_prefix_close, dev_empty, dev_tensor, forced, skel, to
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
-SCAN_CONFIGS = [(0, 4), (0, 2), (1, 4), (1, 2), (1, 8), (2, 4), (2, 8)]
+SCAN_CONFIGS = [(0, 4), (0, 2), (1, 4), (1, 2), (1, 8), (2, 4), (2, 8), (3, 4), (3, 2), (3, 8)]
 
 
 def mod32(a):
@@ -95,3 +95,24 @@ def test_scan_lookback_repeated_runs_identical_int():
             dout.fill_(-1)
             sk.skel_scan("add", True, dx, wrap(dout))
             assert np.array_equal(to_np(dout), ref)
+
+
+@pytest.mark.parametrize("variant", [1, 3])
+def test_scan_types_interleaved_share_lookback_words(variant):
+    """int32 and float32 look-back scans alternate on one stream and reuse the
+    same descriptor words; a stale word of one type must never read as a
+    published value for the other (tested over many calls and tile counts)."""
+    import torch
+    sk = skel()
+    for k in range(12):
+        n = 3_000_001 - 4096 * k
+        xi = syn.uniform_int(700 + k, n, 0, 100)
+        xf = syn.uniform_f32(800 + k, n)
+        oi = dev_empty((n,), torch.int32)
+        of = dev_empty((n,), torch.float32)
+        with forced("scan", variant):
+            sk.skel_scan("add", True, wrap(dev_tensor(xi)), wrap(oi))
+            sk.skel_scan("add", k % 2 == 0, wrap(dev_tensor(xf)), wrap(of))
+        assert np.array_equal(to_np(oi), mod32(oracle.scan_i32(xi, True)))
+        ref, ab = oracle.scan_f32(xf, k % 2 == 0)
+        assert_prefix_close(to_np(of), ref, ab, f"interleaved f32 call {k}")
