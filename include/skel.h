@@ -238,6 +238,30 @@ int skel_mapreduce(skel_fn map_fn, skel_fn red_op, const skel_handle *ins, int n
  * out must not be the same container as in. */
 int skel_scan(skel_fn op, int inclusive, skel_handle in, skel_handle out, void *stream);
 
+/* Allocation-free scan.  The paper has no counterpart to this entry point; it
+ * exists for callers that cannot allocate device memory: a host that hands
+ * the library a fixed memory budget and owns every allocation itself, or a
+ * latency-critical host path that must not take an allocator's lock or risk
+ * the device-wide synchronisation that cudaMalloc and cudaFree can cause.
+ * It computes what skel_scan computes for a 1D operand (op ADD, inclusive or
+ * exclusive, dtype SKEL_I32 wrapping modulo 2^32 or SKEL_F32 with a float64
+ * carry), but on raw device pointers and without containers: `in` and `out`
+ * are caller-owned device arrays of n elements of `dtype` that must not
+ * overlap.  The call allocates nothing: its scratch (a tile counter and the
+ * look-back words) is a static device array of 512 KiB + 256 bytes inside
+ * libskel.so, which every GPU that loads the library holds until the process
+ * exits.  n must be <= SKEL_SCAN_NOALLOC_MAX_N (2^27, the array's capacity);
+ * larger n returns SKEL_ERR_SHAPE without launching.  The first call on each
+ * device looks up the array's device address and clears it (stream-ordered
+ * on `stream`); make that first call before any stream capture.  Every call
+ * shares the array and each leaves it ready for the next, so calls that
+ * overlap on the GPU (on two streams at once, or from two threads) race on
+ * it and must be serialised by the caller.  Enqueued on `stream`; returns
+ * without waiting. */
+#define SKEL_SCAN_NOALLOC_MAX_N ((int64_t)1 << 27)
+int skel_scan_noalloc(skel_fn op, int inclusive, skel_dtype dtype, const void *in, void *out, int64_t n,
+                      void *stream);
+
 /* MapOverlap (SkePU mapoverlap, Sec. III): each output reads a fixed
  * neighbourhood of its input position.
  *   1D (in is 1D), fn = STENCIL1D: out[i] = sum_{k=-r..r} w[k+r] * in[b(i+k)],

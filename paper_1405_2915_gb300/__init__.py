@@ -254,6 +254,17 @@ def skel_scan(op, inclusive: bool, x: Container, out: Container, stream=None) ->
     check(lib.skel_scan(_fn(op), int(inclusive), x.handle, out.handle, _stream(stream)))
 
 
+def skel_scan_noalloc(op, inclusive: bool, x, out, stream=None) -> None:
+    """Allocation-free scan of a contiguous 1D CUDA tensor (float32 or int32)
+    into `out` (same dtype and length); see skel_scan_noalloc in skel.h."""
+    torch = _torch()
+    dt = {torch.float32: F32, torch.int32: I32}[x.dtype]
+    if out.dtype != x.dtype or out.numel() != x.numel() or not x.is_contiguous() or not out.is_contiguous():
+        raise ValueError("skel_scan_noalloc: contiguous tensors of equal dtype and length")
+    check(lib.skel_scan_noalloc(_fn(op), int(inclusive), dt, C.c_void_p(x.data_ptr()), C.c_void_p(out.data_ptr()),
+                                x.numel(), _stream(stream)))
+
+
 def skel_mapoverlap(fn, radius: int, weights, boundary, x: Container, out: Container, stream=None) -> None:
     w = _weights(weights)
     check(lib.skel_mapoverlap(_fn(fn), radius, w[0], w[1], BOUNDARY[boundary] if isinstance(boundary, str) else boundary,

@@ -49,6 +49,7 @@ SIGNATURES = {
     "skel_reduce": (i32, [i32, vp, vp, vp, vp]),
     "skel_mapreduce": (i32, [i32, i32, C.POINTER(vp), i32, vp, vp, vp]),
     "skel_scan": (i32, [i32, i32, vp, vp, vp]),
+    "skel_scan_noalloc": (i32, [i32, i32, i32, vp, vp, i64, vp]),
     "skel_mapoverlap": (i32, [i32, i32, f32p, i32, i32, vp, vp, vp]),
     "skel_maparray": (i32, [i32, vp, vp, vp, vp]),
     "skel_batched": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp]),
