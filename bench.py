@@ -195,6 +195,24 @@ def run_steps(torch, calls, steps, stream, per_call=True):
     return start.elapsed_time(end), per
 
 
+def max_over_ranks(ms: float, device: str = "cuda") -> float:
+    """The slowest rank's time (the whole job is done when the last rank
+    is); a single process returns its own time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(step_bytes: int, world: int, steps: int, ms_max: float) -> float:
+    """Aggregate GB/s over all ranks: every rank moves step_bytes per step
+    (weak scaling), and the job takes the slowest rank's time."""
+    return world * step_bytes * steps / (ms_max * 1e-3) / 1e9
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -441,13 +459,9 @@ def main():
     barrier()
     clocks = sampler.stop()
     sk.skel_check_device()
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms)
     ms_step = t_max / args.steps
-    value = world * step_bytes / (ms_step * 1e-3) / 1e9
+    value = whole_job_gbs(step_bytes, world, args.steps, t_max)
 
     # the fixed default variants (empty table), same steps
     if args.only:

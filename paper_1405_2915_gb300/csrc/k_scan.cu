@@ -15,10 +15,12 @@
 //   2 one_block         one block walks the tiles in order with a carried
 //                       prefix (small n: no inter-block traffic at all).
 //   3 lookback_block    variant 1 with the whole block walking the look-back,
-//                       one predecessor per thread (256 per round): with many
-//                       tiles in flight the nearest published prefix lies far
-//                       back, and warp 0 alone needs many rounds while the
-//                       other warps wait at the barrier.
+//                       one predecessor per thread (256 per round).
+//   4 lookback_tma      persistent blocks, each with four tiles in flight in
+//                       shared-memory stages filled by bulk copies
+//                       (cp.async.bulk + mbarrier), so HBM reads continue
+//                       while a block waits in its look-back (forward scans,
+//                       16-byte aligned operands).
 // ept selects V, the 16-byte groups per thread (tile = 256 threads x 4V).
 // float32: element arithmetic is float32; the prefix carried from tile to
 // tile is float64 (one add per tile), rounded to float32 once per tile.
@@ -95,6 +97,139 @@ scan_lookback(const T *__restrict__ in, T *__restrict__ out, SegGeom g,
     }
     dev::tile_add_prefix<T, V>(v, dev::to_elem<T>(p));
     dev::tile_store<T, kBlock, V>(out, m, v);
+}
+
+// ------------------------------------------------ variant 4: TMA pipeline --
+// A persistent block keeps kStages tiles in flight: thread 0 draws tickets in
+// order and starts a bulk copy (cp.async.bulk, completing on the stage's
+// mbarrier) of each drawn tile into a shared-memory stage; the block consumes
+// the stages in ticket order -- reads the tile from shared memory, refills
+// the stage with the next ticket, scans, walks the look-back, stores.  HBM
+// reads continue while the block waits in its look-back.  A block processes
+// its tickets in increasing order and a tile waits only on smaller tickets,
+// so the smallest unfinished tile always progresses.
+constexpr int kStages = 4;
+constexpr int kTmaV = 4;
+constexpr int kTmaTile = kBlock * 4 * kTmaV;             // 4096 elements = 16 KiB
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+}
+
+// Thread 0: draws the next ticket for stage s and starts its copy.
+template <class T>
+__device__ __forceinline__ void tma_issue(const T *in, const SegGeom &g, Control *ctl, int s, unsigned char *bufs,
+                                          uint64_t *bars, int64_t *tile_of)
+{
+    const int64_t t = (int64_t)atomicAdd(&ctl->ticket, 1u);
+    tile_of[s] = t;
+    if (t >= g.ntiles) return;
+    int64_t first;
+    const TileMap m = tile_map<kTmaTile>(g, t, &first);
+    const uint32_t bytes = (uint32_t)((m.len * (int64_t)sizeof(T)) & ~(int64_t)15);   // whole 16-byte groups
+    const uint32_t bar = smem_u32(bars + s);
+    if (bytes == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bar) : "memory");
+        return;
+    }
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_u32(bufs + (size_t)s * kTmaTile * sizeof(T))), "l"(in + m.base), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+template <class T, bool INCL>
+__global__ void __launch_bounds__(kBlock)
+scan_tma(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc d, Control *ctl, uint32_t epoch,
+         int64_t skip_tile, uint64_t limit_ns)
+{
+    using CT = typename ScanTypes<T>::CT;
+    using V4 = typename ScanTypes<T>::V4;
+    extern __shared__ __align__(1024) unsigned char bufs[];   // kStages tiles
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ int64_t tile_of[kStages];
+    __shared__ T smem[kBlock / 32 + 1];
+    __shared__ CT s_prefix;
+    __shared__ int s_bad;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(bars + s);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_bad = 0;
+        for (int s = 0; s < kStages; ++s) tma_issue<T>(in, g, ctl, s, bufs, bars, tile_of);
+    }
+    __syncthreads();
+    for (uint32_t it = 0;; ++it) {
+        const int s = it % kStages;
+        const uint32_t parity = (it / kStages) & 1u;
+        const int64_t tile = tile_of[s];
+        if (tile >= g.ntiles) break;                          // block-uniform
+        int64_t first;
+        const TileMap m = tile_map<kTmaTile>(g, tile, &first);
+        // wait for the stage's copy (bounded)
+        uint32_t done = 0;
+        for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(smem_u32(bars + s)), "r"(parity) : "memory");
+        if (!done) s_bad = 1;                                 // benign race: every writer stores 1
+        // read the tile in the striped order of tile_scan_local (conflict-free 16-byte reads)
+        const T *buf = reinterpret_cast<const T *>(bufs + (size_t)s * kTmaTile * sizeof(T));
+        const int64_t whole = m.len & ~(int64_t)3;            // elements delivered by the copy
+        T v[kTmaV][4];
+#pragma unroll
+        for (int k = 0; k < kTmaV; ++k) {
+            const int e = w * 128 * kTmaV + k * 128 + lane * 4;
+            if (e + 3 < whole) {
+                const V4 q = *reinterpret_cast<const V4 *>(buf + e);
+                v[k][0] = q.x; v[k][1] = q.y; v[k][2] = q.z; v[k][3] = q.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    v[k][j] = e + j < whole ? buf[e + j] : (e + j < m.len ? in[m.base + e + j] : T(0));
+            }
+        }
+        __syncthreads();                                      // the stage is consumed
+        if (s_bad) {                                          // block-uniform after the barrier
+            if (threadIdx.x == 0) {
+                atomicOr(&ctl->error, kErrTimeout);
+                // wait (bounded) for this block's other copies still in flight
+                for (uint32_t i2 = it + 1; i2 < it + kStages; ++i2) {
+                    const int s2 = i2 % kStages;
+                    if (tile_of[s2] >= g.ntiles) continue;
+                    uint32_t ok = 0;
+                    for (uint32_t k = 0; k < (1u << 22) && !ok; ++k)
+                        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                                     : "=r"(ok) : "r"(smem_u32(bars + s2)), "r"((i2 / kStages) & 1u) : "memory");
+                }
+            }
+            break;
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before the async refill
+            tma_issue<T>(in, g, ctl, s, bufs, bars, tile_of);
+        }
+        const T agg = dev::tile_scan_local<T, INCL, kBlock, kTmaV>(v, smem);
+        if (threadIdx.x < 32) {
+            const CT p = dev::lookback<CT>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, tile != skip_tile);
+            if (threadIdx.x == 0) s_prefix = p;
+        }
+        __syncthreads();
+        dev::tile_add_prefix<T, kTmaV>(v, dev::to_elem<T>(s_prefix));
+        dev::tile_store<T, kBlock, kTmaV>(out, m, v);
+    }
+    // on the normal exit no copy is in flight: tickets are drawn in order, so
+    // once a stage holds an invalid ticket every later stage does too
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t prev = atomicAdd(&ctl->exited, 1u);
+        if (prev == gridDim.x - 1) {   // every block has drawn its last ticket
+            ctl->ticket = 0u;
+            ctl->exited = 0u;
+        }
+    }
 }
 
 // Variant 0, kernel 1: per-tile aggregate (the tile is scanned to obtain it
@@ -241,8 +376,50 @@ int run_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 }
 
 template <class T, bool INCL>
+int run_scan_tma(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+{
+    const T *in = static_cast<const T *>(sc.in);
+    T *out = static_cast<T *>(sc.out);
+    if (sc.reverse) return fail(SKEL_ERR_UNSUPPORTED, "scan tma: forward scans only");
+    if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan tma: ept must be 4");
+    SegGeom g;
+    g.seglen = sc.seg > 0 ? sc.seg : sc.n;
+    g.tps = ceil_div(g.seglen, kTmaTile);
+    g.ntiles = g.tps * (sc.n / g.seglen);
+    g.rev = false;
+    // bulk copies start on 16-byte boundaries: aligned pointers, segments of a multiple of 4 elements
+    if (!aligned16(in) || !aligned16(out) || (sc.seg > 0 && g.seglen % 4))
+        return fail(SKEL_ERR_UNSUPPORTED, "scan tma: 16-byte aligned operands and segments needed");
+    g.vec_ok = true;
+    if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
+    auto kern = scan_tma<T, INCL>;
+    const int dyn = kStages * kTmaTile * (int)sizeof(T);
+    static thread_local bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return fail_cuda(e, "scan tma: shared memory opt-in");
+        attr_set = true;
+    }
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, dyn);
+    if (e != cudaSuccess || occ < 1) return fail(SKEL_ERR_UNSUPPORTED, "scan tma: kernel does not fit an SM");
+    int64_t grid = (int64_t)device_info().sms * occ;
+    if (grid > g.ntiles) grid = g.ntiles;
+    Scratch scr{};
+    int rc = get_scratch(s, 0, 2 * (size_t)g.ntiles, &scr);
+    if (rc) return rc;
+    LookbackDesc d{scr.words, scr.words + g.ntiles};
+    const DebugKnobs k = debug_knobs();
+    launch_kernel(kern, (unsigned)grid, kBlock, (size_t)dyn, s, in, out, g, d, scr.ctl, scr.epoch,
+                  k.scan_skip_publish_tile, k.wait_limit_ns);
+    e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan tma launch");
+}
+
+template <class T, bool INCL>
 int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
+    if (c.variant == 4) return run_scan_tma<T, INCL>(sc, c, s);
     const int v = c.ept > 0 ? c.ept : 4;
     switch (v) {
     case 2: return run_scan<T, INCL, 2>(sc, c, s);
@@ -254,18 +431,18 @@ int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 
 }  // namespace
 
-int scan_variant_count() { return 4; }
+int scan_variant_count() { return 5; }
 const char *scan_variant_name(int v)
 {
-    static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block"};
-    return v >= 0 && v < 4 ? names[v] : "?";
+    static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block", "lookback_tma"};
+    return v >= 0 && v < 5 ? names[v] : "?";
 }
 Choice scan_default() { return Choice{0, 256, 4, 0}; }
 
 int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (sc.n == 0) return SKEL_OK;
-    if (c.variant < 0 || c.variant > 3) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
+    if (c.variant < 0 || c.variant > 4) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "scan: block must be 256");
     if (sc.seg > 0 && sc.n % sc.seg) return fail(SKEL_ERR_SHAPE, "scan: n is not a multiple of the segment");
     if (sc.dtype == SKEL_F32)

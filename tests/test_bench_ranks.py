@@ -1,0 +1,63 @@
+"""The N > 1 path of bench.py on CPU: two gloo ranks, each reporting its own
+time; the job time is the slowest rank's and the throughput counts the work
+of every rank (independent replicas, no data-path collective).  Also checks
+that the reference arm runs on rank 0 only."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    my_ms = 10.0 + 5.0 * rank              # rank 1 is the slow one
+    t = bench.max_over_ranks(my_ms, device="cpu")
+    gbs = bench.whole_job_gbs(step_bytes=10**9, world=world, steps=2, ms_max=t)
+    q.put((rank, t, gbs))
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_whole_job_value_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, t, gbs in res:
+        assert t == 15.0                                     # slowest rank
+        assert abs(gbs - 2 * 10**9 * 2 / 15e-3 / 1e9) < 1e-9   # both ranks' work / slowest time
+
+
+def test_single_process_is_its_own_max():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_reference_arm_nonzero_rank_exits_quietly():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "3"], capture_output=True, text=True, env=env, timeout=120)
+    assert r.returncode == 0
+    assert r.stdout.strip() == ""
