@@ -21,6 +21,9 @@
 //                       (cp.async.bulk + mbarrier), so HBM reads continue
 //                       while a block waits in its look-back (forward scans,
 //                       16-byte aligned operands).
+//   5 lookback_big      64 KiB tiles staged in shared memory by bulk copies,
+//                       scanned in place, with all warps walking the
+//                       look-back (forward scans, 16-byte aligned operands).
 // ept selects V, the 16-byte groups per thread (tile = 256 threads x 4V).
 // float32: element arithmetic is float32; the prefix carried from tile to
 // tile is float64 (one add per tile), rounded to float32 once per tile.
@@ -232,6 +235,125 @@ scan_tma(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     }
 }
 
+// ------------------------------------------- variant 5: big staged tiles --
+// One block per 64 KiB tile (four sub-tiles of 4096 elements), drawn in
+// ticket order.  The tile arrives by bulk copies into shared memory; each
+// sub-tile is scanned in place (registers -> shared memory, the same rounding
+// depth as one 4096-element tile), the tile aggregate is published, the
+// look-back is walked by all warps (one window of 32 each per round), and
+// the prefix is added while the tile is stored.  Four times fewer tiles per
+// byte than the 16 KiB tiles means a four times shorter look-back walk.
+constexpr int kBigSub = 4;
+constexpr int kBigTile = kBigSub * kTmaTile;            // 16384 elements
+
+template <class T, bool INCL>
+__global__ void __launch_bounds__(kBlock)
+scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc d, Control *ctl, uint32_t epoch,
+         int64_t skip_tile, uint64_t limit_ns)
+{
+    using CT = typename ScanTypes<T>::CT;
+    using V4 = typename ScanTypes<T>::V4;
+    extern __shared__ __align__(1024) unsigned char dyn[];   // kBigTile elements
+    T *buf = reinterpret_cast<T *>(dyn);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int64_t s_tile;
+    __shared__ T smem[kBlock / 32 + 1];
+    __shared__ dev::WideLookbackSmem<CT, kBlock / 32> lbs;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(&ctl->ticket, 1u);
+        if ((int64_t)t == g.ntiles - 1) ctl->ticket = 0u;   // the last ticket: every block has drawn
+        s_tile = t;
+        mbar_init(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        int64_t first0;
+        const TileMap m0 = tile_map<kBigTile>(g, t, &first0);
+        const uint32_t bytes = (uint32_t)((m0.len * (int64_t)sizeof(T)) & ~(int64_t)15);
+        const uint32_t b = smem_u32(&bar);
+        if (bytes == 0) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
+        } else {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
+            for (uint32_t c = 0; c < bytes; c += 16384u) {
+                const uint32_t sz = bytes - c < 16384u ? bytes - c : 16384u;
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(smem_u32(dyn + c)), "l"(reinterpret_cast<const unsigned char *>(in + m0.base) + c),
+                                "r"(sz), "r"(b)
+                             : "memory");
+            }
+        }
+    }
+    __syncthreads();
+    const int64_t tile = s_tile;
+    int64_t first;
+    const TileMap m = tile_map<kBigTile>(g, tile, &first);
+    uint32_t done = 0;
+    for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
+    if (!__syncthreads_and(done)) {
+        if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+        // wait once more (bounded) for the copy still in flight into this block's shared memory
+        for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
+        return;   // the tile is never published: its successors' bounded waits give up
+    }
+    const int64_t whole = m.len & ~(int64_t)3;
+    // pass A: scan every sub-tile in place; carries between sub-tiles in CT
+    CT carry[kBigSub];
+    CT run = CT(0);
+#pragma unroll
+    for (int j = 0; j < kBigSub; ++j) {
+        carry[j] = run;
+        const int64_t off = (int64_t)j * kTmaTile;
+        if (off >= m.len) continue;                          // block-uniform
+        T v[kTmaV][4];
+#pragma unroll
+        for (int k = 0; k < kTmaV; ++k) {
+            const int64_t e = off + w * 128 * kTmaV + k * 128 + lane * 4;
+            if (e + 3 < whole) {
+                const V4 q = *reinterpret_cast<const V4 *>(buf + e);
+                v[k][0] = q.x; v[k][1] = q.y; v[k][2] = q.z; v[k][3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    v[k][i] = e + i < whole ? buf[e + i] : (e + i < m.len ? in[m.base + e + i] : T(0));
+            }
+        }
+        const T agg = dev::tile_scan_local<T, INCL, kBlock, kTmaV>(v, smem);
+#pragma unroll
+        for (int k = 0; k < kTmaV; ++k) {
+            const int64_t e = off + w * 128 * kTmaV + k * 128 + lane * 4;   // the same slots this thread read
+            V4 q;
+            q.x = v[k][0]; q.y = v[k][1]; q.z = v[k][2]; q.w = v[k][3];
+            *reinterpret_cast<V4 *>(buf + e) = q;
+        }
+        run = run + (CT)agg;
+    }
+    const CT p = dev::wide_lookback<CT, kBlock / 32>(tile, first, run, d, epoch, ctl, limit_ns, tile != skip_tile, lbs);
+    // pass B: add the prefix and store, sub-tile by sub-tile
+#pragma unroll
+    for (int j = 0; j < kBigSub; ++j) {
+        const int64_t off = (int64_t)j * kTmaTile;
+        if (off >= m.len) continue;
+        T v[kTmaV][4];
+#pragma unroll
+        for (int k = 0; k < kTmaV; ++k) {
+            const int64_t e = off + w * 128 * kTmaV + k * 128 + lane * 4;
+            const V4 q = *reinterpret_cast<const V4 *>(buf + e);
+            v[k][0] = q.x; v[k][1] = q.y; v[k][2] = q.z; v[k][3] = q.w;
+        }
+        dev::tile_add_prefix<T, kTmaV>(v, dev::to_elem<T>(p + carry[j]));
+        TileMap ms;
+        ms.base = m.base + off;
+        ms.len = m.len - off < kTmaTile ? m.len - off : kTmaTile;
+        ms.rev = false;
+        ms.vec = ms.len == kTmaTile;
+        dev::tile_store<T, kBlock, kTmaV>(out, ms, v);
+    }
+}
+
 // Variant 0, kernel 1: per-tile aggregate (the tile is scanned to obtain it
 // in the same order the apply kernel uses).
 template <class T, int V>
@@ -417,9 +539,45 @@ int run_scan_tma(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 }
 
 template <class T, bool INCL>
+int run_scan_big(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+{
+    const T *in = static_cast<const T *>(sc.in);
+    T *out = static_cast<T *>(sc.out);
+    if (sc.reverse) return fail(SKEL_ERR_UNSUPPORTED, "scan big: forward scans only");
+    if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan big: ept must be 4");
+    SegGeom g;
+    g.seglen = sc.seg > 0 ? sc.seg : sc.n;
+    g.tps = ceil_div(g.seglen, kBigTile);
+    g.ntiles = g.tps * (sc.n / g.seglen);
+    g.rev = false;
+    if (!aligned16(in) || !aligned16(out) || (sc.seg > 0 && g.seglen % 4))
+        return fail(SKEL_ERR_UNSUPPORTED, "scan big: 16-byte aligned operands and segments needed");
+    g.vec_ok = true;
+    if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
+    auto kern = scan_big<T, INCL>;
+    const int dyn = kBigTile * (int)sizeof(T);
+    static thread_local bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+        if (e != cudaSuccess) return fail_cuda(e, "scan big: shared memory opt-in");
+        attr_set = true;
+    }
+    Scratch scr{};
+    int rc = get_scratch(s, 0, 2 * (size_t)g.ntiles, &scr);
+    if (rc) return rc;
+    LookbackDesc d{scr.words, scr.words + g.ntiles};
+    const DebugKnobs k = debug_knobs();
+    launch_kernel(kern, (unsigned)g.ntiles, kBlock, (size_t)dyn, s, in, out, g, d, scr.ctl, scr.epoch,
+                  k.scan_skip_publish_tile, k.wait_limit_ns);
+    cudaError_t e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan big launch");
+}
+
+template <class T, bool INCL>
 int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (c.variant == 4) return run_scan_tma<T, INCL>(sc, c, s);
+    if (c.variant == 5) return run_scan_big<T, INCL>(sc, c, s);
     const int v = c.ept > 0 ? c.ept : 4;
     switch (v) {
     case 2: return run_scan<T, INCL, 2>(sc, c, s);
@@ -431,18 +589,19 @@ int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 
 }  // namespace
 
-int scan_variant_count() { return 5; }
+int scan_variant_count() { return 6; }
 const char *scan_variant_name(int v)
 {
-    static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block", "lookback_tma"};
-    return v >= 0 && v < 5 ? names[v] : "?";
+    static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block", "lookback_tma",
+                                  "lookback_big"};
+    return v >= 0 && v < 6 ? names[v] : "?";
 }
 Choice scan_default() { return Choice{0, 256, 4, 0}; }
 
 int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (sc.n == 0) return SKEL_OK;
-    if (c.variant < 0 || c.variant > 4) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
+    if (c.variant < 0 || c.variant > 5) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "scan: block must be 256");
     if (sc.seg > 0 && sc.n % sc.seg) return fail(SKEL_ERR_SHAPE, "scan: n is not a multiple of the segment");
     if (sc.dtype == SKEL_F32)

@@ -275,5 +275,85 @@ __device__ __forceinline__ CT block_lookback(int64_t tile, int64_t first, CT agg
     return excl;
 }
 
+// Wide variant: each of the NW warps polls its own window of 32 predecessors
+// (warp w: pred - 32w - lane) until the window is ready up to its nearest
+// published prefix, so one round reads 32*NW predecessors with one barrier.
+// Warps farther back wait on older tiles, which are the likeliest to be
+// ready.  Returns the exclusive prefix in every thread.
+template <class CT, int NW>
+struct WideLookbackSmem {
+    CT sum[NW];
+    int incl[NW];     // 1 if the warp's window holds a published prefix
+    CT result;
+};
+
+template <class CT, int NW>
+__device__ __forceinline__ CT wide_lookback(int64_t tile, int64_t first, CT agg, LookbackDesc d, uint32_t epoch,
+                                            Control *ctl, uint64_t limit_ns, bool publish,
+                                            WideLookbackSmem<CT, NW> &sm)
+{
+    constexpr int W = Codec<CT>::W;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (tile == first) {
+        if (publish && threadIdx.x == 0) Codec<CT>::put(d.incl + tile * W, agg, epoch);
+        return CT(0);
+    }
+    if (publish && threadIdx.x == 0) Codec<CT>::put(d.agg + tile * W, agg, epoch);
+    CT excl = CT(0);
+    int64_t pred = tile - 1;
+    uint64_t t0 = 0;
+    bool gave_up = false;
+    while (true) {
+        const int64_t p = pred - 32 * w - lane;
+        const bool inseg = p >= first;
+        uint32_t status = 0;
+        unsigned incl_mask = 0;
+        CT val = CT(0);
+        while (true) {
+            if (inseg) status = peek<CT>(d, p, epoch, val);
+            else { status = kStIncl; val = CT(0); }
+            const unsigned ready_mask = __ballot_sync(0xffffffffu, status != 0);
+            incl_mask = __ballot_sync(0xffffffffu, status == kStIncl);
+            const unsigned need = incl_mask ? (((incl_mask & (0u - incl_mask)) << 1) - 1u) : 0xffffffffu;
+            if ((ready_mask & need) == need || gave_up) break;
+            if (t0 == 0) t0 = globaltimer();
+            bool expired = (globaltimer() - t0 > limit_ns) || ld_volatile(&ctl->abort) == epoch;
+            expired = __any_sync(0xffffffffu, expired);
+            if (expired) {
+                if (lane == 0) {
+                    atomicOr(&ctl->error, kErrTimeout);
+                    atomicExch(&ctl->abort, epoch);
+                }
+                gave_up = true;
+            }
+        }
+        const unsigned lim = incl_mask ? (((incl_mask & (0u - incl_mask)) << 1) - 1u) : 0xffffffffu;
+        if (!((lim >> lane) & 1u) || status == 0) val = CT(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val = val + shfl_xor_ct(val, o);
+        if (lane == 0) {
+            sm.sum[w] = val;
+            sm.incl[w] = incl_mask != 0u;
+        }
+        __syncthreads();
+        // nearest window with a published prefix; sum the windows up to it
+        CT s = CT(0);
+        bool found = false;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            if (!found) {
+                s = s + sm.sum[k];
+                found = sm.incl[k] != 0;
+            }
+        }
+        excl = excl + s;
+        __syncthreads();   // sm is rewritten by the next round
+        if (found) break;
+        pred -= 32 * NW;
+    }
+    if (publish && threadIdx.x == 0) Codec<CT>::put(d.incl + tile * W, excl + agg, epoch);
+    return excl;
+}
+
 }  // namespace dev
 }  // namespace skel

@@ -83,6 +83,7 @@ def candidates(sk_name: str):
             for e in (2, 4, 8):
                 yield (v, 256, e, 0)
         yield (4, 256, 4, 0)
+        yield (5, 256, 4, 0)
     elif sk_name == "mapoverlap2d":
         yield (0, 256, 0, 0)
         yield (1, 256, 0, 0)

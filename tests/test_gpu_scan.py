@@ -11,7 +11,7 @@ from helpers import assert_prefix_close, dev_empty, dev_tensor, forced, skel, to
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
-SCAN_CONFIGS = [(0, 4), (0, 2), (1, 4), (1, 2), (1, 8), (2, 4), (2, 8), (3, 4), (3, 2), (3, 8), (4, 4)]
+SCAN_CONFIGS = [(0, 4), (0, 2), (1, 4), (1, 2), (1, 8), (2, 4), (2, 8), (3, 4), (3, 2), (3, 8), (4, 4), (5, 4)]
 
 
 def mod32(a):
@@ -29,7 +29,7 @@ def test_scan_i32_exact(variant, ept, n, inclusive, pad):
     dx = dev_tensor(x, pad)
     dout = dev_empty((n,), torch.int32, pad)
     with forced("scan", variant, 0, ept):
-        if variant == 4 and pad % 4:
+        if variant in (4, 5) and pad % 4:
             # bulk copies need 16-byte aligned operands; a forced call does not fall back
             with pytest.raises(sk.SkelError) as e:
                 sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
@@ -103,7 +103,7 @@ def test_scan_lookback_repeated_runs_identical_int():
             assert np.array_equal(to_np(dout), ref)
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4])
+@pytest.mark.parametrize("variant", [1, 3, 4, 5])
 def test_scan_types_interleaved_share_lookback_words(variant):
     """int32 and float32 look-back scans alternate on one stream and reuse the
     same descriptor words; a stale word of one type must never read as a
@@ -124,16 +124,17 @@ def test_scan_types_interleaved_share_lookback_words(variant):
         assert_prefix_close(to_np(of), ref, ab, f"interleaved f32 call {k}")
 
 
-@pytest.mark.parametrize("rows,cols", [(3, 5000), (7, 4096), (64, 1000), (2, 12)])
+@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("rows,cols", [(3, 5000), (7, 4096), (64, 1000), (2, 12), (3, 40000)])
 @pytest.mark.parametrize("inclusive", [True, False])
-def test_scan_rows_tma(rows, cols, inclusive):
-    """Row-wise scans through the bulk-copy pipeline (segments of a multiple
+def test_scan_rows_tma(variant, rows, cols, inclusive):
+    """Row-wise scans through the bulk-copy variants (segments of a multiple
     of 4 elements)."""
     import torch
     sk = skel()
     x = syn.uniform_f32(43, rows * cols).reshape(rows, cols)
     dout = dev_empty((rows, cols), torch.float32)
-    with forced("scan", 4):
+    with forced("scan", variant):
         sk.skel_scan("add", inclusive, wrap(dev_tensor(x)), wrap(dout))
     g = to_np(dout)
     for r in range(rows):
