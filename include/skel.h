@@ -345,7 +345,8 @@ int skel_mapoverlap_bwd(skel_fn fn, int radius, const float *weights, int nweigh
 /* Loads an execution-plan table (text, one entry per line; see the table
  * writer of the autotuner):
  *   skeleton fn dtype bucket radius residency variant block ept tile
- * bucket = floor(log2(n) / 2) (n elements; n = 0 uses bucket 0).  Entries
+ * bucket = floor(log2(n) / 2) (n elements; n = 0 uses bucket 0); variant -1
+ * records that the built-in default is the best choice for that key.  Entries
  * replace the built-in defaults for their key; a call whose key has no entry
  * uses the entry of the nearest lower tuned bucket of the same (skeleton, fn,
  * dtype, radius, residency), else the nearest higher one, else the built-in

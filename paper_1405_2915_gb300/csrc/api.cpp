@@ -948,7 +948,8 @@ int skel_scan_bwd(skel_fn op, int inclusive, skel_handle gout, skel_handle gin, 
         if (rc) return rc;
         ScanLaunch sc{SKEL_F32, inclusive != 0, true, ops[0].ptr, ops[1].ptr, gout->n,
                       gout->ndim == 2 ? gout->shape[1] : 0};
-        Context ctx{SKEL_SK_SCAN, inclusive ? 1 : 0, SKEL_F32, gout->ndim == 2 ? gout->shape[1] : gout->n, 0, res};
+        // reverse scans have their own keys (fn 2: exclusive, 3: inclusive)
+        Context ctx{SKEL_SK_SCAN, inclusive ? 3 : 2, SKEL_F32, gout->ndim == 2 ? gout->shape[1] : gout->n, 0, res};
         return run_with_fallback(SKEL_SK_SCAN, ctx, [&](const Choice &c) { return launch_scan(sc, c, s); }, scan_def);
     });
 }

@@ -15,10 +15,16 @@
 //           scans them, sums their squares, and finds both prefixes with a
 //           look-back over the earlier tiles of its instance, carrying the
 //           pair in float64.  The last tile of an instance writes its sum.
-// Variants: 0 persistent (grid = SMs x resident blocks per SM), look-back
-//             walked by warp 0;
-//           1 one_per_tile (grid = the tile bound; surplus blocks exit);
-//           2 persistent with the whole block walking the look-back.
+// Variants: 0 persistent (grid = SMs x resident blocks per SM); the tile's
+//             aggregate is published right after its load, and all warps
+//             walk the look-back in parallel windows;
+//           1 one_per_tile (grid = the tile bound; surplus blocks exit),
+//             otherwise as 0;
+//           2 persistent with the whole block walking the look-back, one
+//             predecessor per thread;
+//           3 big_tile: 64 KiB frames staged by bulk copies, aggregates
+//             published before the scans, all warps walking the look-back;
+//           4 persistent with warp 0 alone walking the look-back.
 #include "scan_tile.cuh"
 
 namespace skel {
@@ -161,9 +167,189 @@ __device__ __forceinline__ void store_masked(float *__restrict__ out, int64_t fb
     }
 }
 
-// BLK: the whole block walks the look-back (variant 2) or warp 0 alone
-// (variants 0, 1).  words: 2 * max_t aggregate words, then 2 * max_t prefix words.
-template <bool SCAN, bool RED, bool INCL, int V, bool BLK>
+// ----------------------------------------------- variant 3: big tiles ----
+// One block per 64 KiB frame of an instance (four 4096-element sub-tiles),
+// drawn in ticket order: the frame [fbase, fbase + 16384) arrives by bulk
+// copies into shared memory (clipped to the values array), the (scan, sum of
+// squares) aggregate is published first, the sub-tiles are scanned in place,
+// all warps walk the look-back over the instance's earlier tiles, and the
+// prefix is added while the instance's elements are stored.
+constexpr int kBigV = 4;
+constexpr int kBigSub = 4;
+constexpr int kSubTile = kBlock * 4 * kBigV;            // 4096
+constexpr int kBigTile = kBigSub * kSubTile;            // 16384 elements
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <bool SCAN, bool RED, bool INCL>
+__global__ void __launch_bounds__(kBlock)
+batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ results,
+            float *__restrict__ scan_out, Layout L, uint64_t *words, int64_t max_t, int64_t total_elems, Control *ctl,
+            uint32_t epoch, uint64_t limit_ns)
+{
+    extern __shared__ __align__(1024) unsigned char dyn[];   // kBigTile floats
+    float *buf = reinterpret_cast<float *>(dyn);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int64_t s_meta[5];   // tile, instance, lo, hi, first
+    __shared__ int64_t s_last;
+    __shared__ float smem[kBlock / 32 + 1];
+    __shared__ float red[32];
+    __shared__ dev::WideLookbackSmem<Pair, kBlock / 32> lbs;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const dev::LookbackDesc d{words, words + 2 * max_t};
+    if (threadIdx.x == 0) {
+        const uint32_t t = atomicAdd(&ctl->queue, 1u);
+        if ((int64_t)t == max_t - 1) ctl->queue = 0u;       // every block of the grid has drawn
+        const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+        s_meta[0] = t;
+        if ((int64_t)t < total) {
+            const int64_t b = L.tile_inst[t];
+            const int64_t lo = off[b], hi = off[b + 1], first = L.tile_start[b];
+            s_meta[1] = b; s_meta[2] = lo; s_meta[3] = hi; s_meta[4] = first;
+            s_last = L.tile_start[b + 1] - 1;
+            const int64_t fbase = (lo & ~(int64_t)3) + ((int64_t)t - first) * kBigTile;
+            int64_t end = fbase + kBigTile < hi ? fbase + kBigTile : hi;
+            end = (end + 3) & ~(int64_t)3;                      // whole 16-byte groups ...
+            if (end > (total_elems & ~(int64_t)3)) end = total_elems & ~(int64_t)3;   // ... inside the array
+            const uint32_t bytes = end > fbase ? (uint32_t)((end - fbase) * 4) : 0u;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            const uint32_t bb = smem_u32(&bar);
+            if (bytes == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bb) : "memory");
+            } else {
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bb), "r"(bytes) : "memory");
+                for (uint32_t c = 0; c < bytes; c += 16384u) {
+                    const uint32_t sz = bytes - c < 16384u ? bytes - c : 16384u;
+                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                                 :: "r"(smem_u32(dyn + c)),
+                                    "l"(reinterpret_cast<const unsigned char *>(values + fbase) + c), "r"(sz), "r"(bb)
+                                 : "memory");
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+    const int64_t t = s_meta[0];
+    if (t >= total) return;                                    // block-uniform: a surplus block
+    const int64_t b = s_meta[1], lo = s_meta[2], hi = s_meta[3], first = s_meta[4], last = s_last;
+    const int64_t fbase = (lo & ~(int64_t)3) + (t - first) * kBigTile;
+    int64_t fend = fbase + kBigTile < hi ? fbase + kBigTile : hi;
+    fend = (fend + 3) & ~(int64_t)3;
+    if (fend > (total_elems & ~(int64_t)3)) fend = total_elems & ~(int64_t)3;   // staged: [fbase, fend)
+    uint32_t done = 0;
+    for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                     : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
+    if (!__syncthreads_and(done)) {
+        if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+        for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
+        return;
+    }
+    // element e of the frame: staged if fbase + e < fend, else read directly;
+    // positions outside [lo, hi) count as 0
+    auto at = [&](int64_t e) -> float {
+        const int64_t p = fbase + e;
+        if (p < lo || p >= hi) return 0.f;
+        return p < fend ? buf[e] : values[p];
+    };
+    // early aggregates: pairwise per thread, then the block trees
+    float ps[kBigSub * kBigV], pq[kBigSub * kBigV];
+#pragma unroll
+    for (int j = 0; j < kBigSub; ++j) {
+#pragma unroll
+        for (int k = 0; k < kBigV; ++k) {
+            const int64_t e = (int64_t)j * kSubTile + w * 128 * kBigV + k * 128 + lane * 4;
+            float a[4];
+            if (fbase + e >= lo && fbase + e + 3 < hi && fbase + e + 3 < fend) {
+                const float4 q = *reinterpret_cast<const float4 *>(buf + e);
+                a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = at(e + i);
+            }
+            ps[j * kBigV + k] = (a[0] + a[1]) + (a[2] + a[3]);
+            pq[j * kBigV + k] = fmaf(a[0], a[0], a[1] * a[1]) + fmaf(a[2], a[2], a[3] * a[3]);
+        }
+    }
+#pragma unroll
+    for (int st = 1; st < kBigSub * kBigV; st *= 2)
+#pragma unroll
+        for (int i = 0; i + st < kBigSub * kBigV; i += 2 * st) {
+            ps[i] = ps[i] + ps[i + st];
+            pq[i] = pq[i] + pq[i + st];
+        }
+    const float agg_s = SCAN ? dev::block_reduce<dev::AddF, float, kBlock>(ps[0], red) : 0.f;
+    const float agg_q = RED ? dev::block_reduce<dev::AddF, float, kBlock>(pq[0], red) : 0.f;
+    const Pair agg((double)agg_s, (double)agg_q);
+    const bool multi = first != last;
+    if (multi && threadIdx.x == 0) {
+        if (t == first) dev::Codec<Pair>::put(d.incl + t * 2, agg, epoch);
+        else dev::Codec<Pair>::put(d.agg + t * 2, agg, epoch);
+    }
+    // pass A: scan the sub-tiles in place
+    double carry[kBigSub];
+    double run = 0.0;
+    if (SCAN) {
+#pragma unroll
+        for (int j = 0; j < kBigSub; ++j) {
+            carry[j] = run;
+            const int64_t o = (int64_t)j * kSubTile;
+            if (fbase + o >= hi) continue;                      // block-uniform
+            float v[kBigV][4];
+#pragma unroll
+            for (int k = 0; k < kBigV; ++k) {
+                const int64_t e = o + w * 128 * kBigV + k * 128 + lane * 4;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[k][i] = at(e + i);
+            }
+            const float sub = dev::tile_scan_local<float, INCL, kBlock, kBigV>(v, smem);
+#pragma unroll
+            for (int k = 0; k < kBigV; ++k) {
+                const int64_t e = o + w * 128 * kBigV + k * 128 + lane * 4;
+                *reinterpret_cast<float4 *>(buf + e) = make_float4(v[k][0], v[k][1], v[k][2], v[k][3]);
+            }
+            run += (double)sub;
+        }
+    }
+    Pair p(0.0);
+    if (multi)
+        p = dev::wide_lookback<Pair, kBlock / 32>(t, first, agg, d, epoch, ctl, limit_ns, false, t != first, lbs);
+    if (RED && t == last && threadIdx.x == 0) results[b] = (float)(p.q + agg.q);
+    if (SCAN) {
+        // pass B: add the prefix and store the instance's elements
+#pragma unroll
+        for (int j = 0; j < kBigSub; ++j) {
+            const int64_t o = (int64_t)j * kSubTile;
+            if (fbase + o >= hi) continue;
+            const float pre = (float)(p.s + carry[j]);
+#pragma unroll
+            for (int k = 0; k < kBigV; ++k) {
+                const int64_t e = o + w * 128 * kBigV + k * 128 + lane * 4;
+                const float4 q = *reinterpret_cast<const float4 *>(buf + e);
+                const float r[4] = {pre + q.x, pre + q.y, pre + q.z, pre + q.w};
+                const int64_t pp = fbase + e;
+                if (pp >= lo && pp + 3 < hi) {
+                    dev::st_stream(reinterpret_cast<float4 *>(scan_out + pp), make_float4(r[0], r[1], r[2], r[3]));
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (pp + i >= lo && pp + i < hi) scan_out[pp + i] = r[i];
+                }
+            }
+        }
+    }
+}
+
+// LB: how the look-back is walked -- 0 by warp 0 alone (variant 4), 1 by
+// the whole block one predecessor per thread (variant 2), 2 by all warps in
+// parallel windows after publishing the tile's aggregate early, from a
+// pairwise sum taken right after the load (variants 0 and 1).
+// words: 2 * max_t aggregate words, then 2 * max_t prefix words.
+template <bool SCAN, bool RED, bool INCL, int V, int LB>
 __global__ void __launch_bounds__(kBlock)
 batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ results,
              float *__restrict__ scan_out, Layout L, uint64_t *words, int64_t max_t, Control *ctl, uint32_t epoch,
@@ -175,6 +361,7 @@ batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, 
     __shared__ int64_t s_tile;
     __shared__ Pair s_prefix;
     __shared__ dev::BlockLookbackSmem<Pair, kBlock> lbs;
+    __shared__ dev::WideLookbackSmem<Pair, kBlock / 32> wls;
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
     const dev::LookbackDesc d{words, words + 2 * max_t};
     while (true) {
@@ -187,22 +374,48 @@ batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, 
         const int64_t first = L.tile_start[b];
         const int64_t last = L.tile_start[b + 1] - 1;
         const int64_t fbase = (lo & ~(int64_t)3) + (t - first) * TILE;
+        const bool multi = first != last;   // block-uniform
         float v[V][4];
         load_masked<V>(values, fbase, lo, hi, v);
-        float q = 0.f;
-        if (RED) {
+        Pair agg(0.0);
+        if (LB == 2) {
+            // pairwise per thread (rounding depth 2 + log2 V), then the block trees
+            float ps[V], pq[V];
 #pragma unroll
-            for (int k = 0; k < V; ++k)
+            for (int k = 0; k < V; ++k) {
+                ps[k] = (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
+                pq[k] = fmaf(v[k][0], v[k][0], v[k][1] * v[k][1]) + fmaf(v[k][2], v[k][2], v[k][3] * v[k][3]);
+            }
 #pragma unroll
-                for (int j = 0; j < 4; ++j) q = fmaf(v[k][j], v[k][j], q);
-            q = dev::block_reduce<dev::AddF, float, kBlock>(q, red_smem);
+            for (int st = 1; st < V; st *= 2)
+#pragma unroll
+                for (int i = 0; i + st < V; i += 2 * st) { ps[i] = ps[i] + ps[i + st]; pq[i] = pq[i] + pq[i + st]; }
+            const float as = SCAN ? dev::block_reduce<dev::AddF, float, kBlock>(ps[0], red_smem) : 0.f;
+            const float aq = RED ? dev::block_reduce<dev::AddF, float, kBlock>(pq[0], red_smem) : 0.f;
+            agg = Pair((double)as, (double)aq);
+            if (multi && threadIdx.x == 0) {
+                if (t == first) dev::Codec<Pair>::put(d.incl + t * 2, agg, epoch);
+                else dev::Codec<Pair>::put(d.agg + t * 2, agg, epoch);
+            }
+            if (SCAN) dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
+        } else {
+            float q = 0.f;
+            if (RED) {
+#pragma unroll
+                for (int k = 0; k < V; ++k)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) q = fmaf(v[k][j], v[k][j], q);
+                q = dev::block_reduce<dev::AddF, float, kBlock>(q, red_smem);
+            }
+            float sagg = 0.f;
+            if (SCAN) sagg = dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
+            agg = Pair((double)sagg, (double)q);
         }
-        float sagg = 0.f;
-        if (SCAN) sagg = dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
-        const Pair agg((double)sagg, (double)q);
         Pair p(0.0);
-        if (first != last) {   // block-uniform
-            if (BLK) {
+        if (multi) {
+            if (LB == 2) {
+                p = dev::wide_lookback<Pair, kBlock / 32>(t, first, agg, d, epoch, ctl, limit_ns, false, t != first, wls);
+            } else if (LB == 1) {
                 p = dev::block_lookback<Pair, kBlock>(t, first, agg, d, epoch, ctl, limit_ns, true, lbs);
             } else {
                 if (threadIdx.x < 32) {
@@ -233,7 +446,9 @@ template <bool SCAN, bool RED, bool INCL, int V>
 int run_main(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, const Layout &L,
              uint32_t epoch, int64_t max_t, cudaStream_t s)
 {
-    auto kern = c.variant == 2 ? batched_main<SCAN, RED, INCL, V, true> : batched_main<SCAN, RED, INCL, V, false>;
+    auto kern = c.variant == 2   ? batched_main<SCAN, RED, INCL, V, 1>
+                : c.variant == 4 ? batched_main<SCAN, RED, INCL, V, 0>
+                                 : batched_main<SCAN, RED, INCL, V, 2>;
     int64_t grid;
     if (c.variant == 1) {
         grid = max_t;
@@ -273,17 +488,51 @@ int run_v(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words
     return run_main<false, true, true, V>(b, c, ctl, words, L, epoch, mt, s);
 }
 
-int tile_of(const Choice &c) { return kBlock * 4 * (c.ept > 0 ? c.ept : 4); }
+int tile_of(const Choice &c) { return c.variant == 3 ? kBigTile : kBlock * 4 * (c.ept > 0 ? c.ept : 4); }
+
+template <bool SCAN, bool RED, bool INCL>
+int run_big_k(const BatchedLaunch &b, Control *ctl, uint64_t *words, const Layout &L, uint32_t epoch, int64_t max_t,
+              cudaStream_t s)
+{
+    auto kern = batched_big<SCAN, RED, INCL>;
+    const int dyn = kBigTile * (int)sizeof(float);
+    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (ea != cudaSuccess) return fail_cuda(ea, "batched big: shared memory opt-in");
+    const DebugKnobs k = debug_knobs();
+    launch_kernel(kern, (unsigned)max_t, kBlock, (size_t)dyn, s, b.values, b.offsets, b.results, b.scan_out, L, words,
+                  max_t, b.total, ctl, epoch, k.wait_limit_ns);
+    cudaError_t e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "batched big launch");
+}
+
+int run_big(const BatchedLaunch &b, Control *ctl, uint64_t *words, unsigned char *data, uint32_t epoch,
+            cudaStream_t s)
+{
+    const Layout L = layout(data, b, kBigTile);
+    const int64_t mt = max_tiles(b, kBigTile);
+    if (mt > 0x7fffffffLL || b.B > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "batched: too many instances or tiles");
+    launch_kernel(batched_prep, 1, 1024, 0, s, b.offsets, b.B, b.total, kBigTile, L, b.results, ctl, mt);
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prep launch");
+    if (b.want_scan && b.want_reduce)
+        return b.inclusive ? run_big_k<true, true, true>(b, ctl, words, L, epoch, mt, s)
+                           : run_big_k<true, true, false>(b, ctl, words, L, epoch, mt, s);
+    if (b.want_scan)
+        return b.inclusive ? run_big_k<true, false, true>(b, ctl, words, L, epoch, mt, s)
+                           : run_big_k<true, false, false>(b, ctl, words, L, epoch, mt, s);
+    return run_big_k<false, true, true>(b, ctl, words, L, epoch, mt, s);
+}
 
 }  // namespace
 
-int batched_variant_count() { return 3; }
+int batched_variant_count() { return 5; }
 const char *batched_variant_name(int v)
 {
-    static const char *names[] = {"persistent", "one_per_tile", "persistent_block_lookback"};
-    return v >= 0 && v < 3 ? names[v] : "?";
+    static const char *names[] = {"persistent", "one_per_tile", "persistent_block_lookback", "big_tile",
+                                  "persistent_warp_lookback"};
+    return v >= 0 && v < 5 ? names[v] : "?";
 }
-Choice batched_default() { return Choice{0, 256, 4, 0}; }
+Choice batched_default() { return Choice{4, 256, 4, 0}; }
 
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c) { return layout_bytes(b, tile_of(c)); }
 // aggregate and prefix of every tile, two words (scan carry, sum of squares) each
@@ -292,11 +541,15 @@ size_t batched_word_count(const BatchedLaunch &b, const Choice &c) { return 4 * 
 int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, unsigned char *data,
                    uint32_t epoch, cudaStream_t s)
 {
-    if (c.variant < 0 || c.variant > 2) return fail(SKEL_ERR_INVALID_ARG, "batched: unknown variant");
+    if (c.variant < 0 || c.variant > 4) return fail(SKEL_ERR_INVALID_ARG, "batched: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "batched: block must be 256");
     if (!aligned16(b.values) || (b.scan_out && !aligned16(b.scan_out)))
         return fail(SKEL_ERR_UNSUPPORTED, "batched: values and scan_out must be 16-byte aligned");
     if (b.B == 0) return SKEL_OK;
+    if (c.variant == 3) {
+        if (c.ept > 0 && c.ept != kBigV) return fail(SKEL_ERR_INVALID_ARG, "batched big: ept must be 4");
+        return run_big(b, ctl, words, data, epoch, s);
+    }
     switch (c.ept > 0 ? c.ept : 4) {
     case 2: return run_v<2>(b, c, ctl, words, data, epoch, s);
     case 4: return run_v<4>(b, c, ctl, words, data, epoch, s);

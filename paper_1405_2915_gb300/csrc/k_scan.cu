@@ -22,11 +22,15 @@
 //                       while a block waits in its look-back (forward scans,
 //                       16-byte aligned operands).
 //   5 lookback_big      64 KiB tiles staged in shared memory by bulk copies,
-//                       scanned in place, with all warps walking the
-//                       look-back (forward scans, 16-byte aligned operands).
+//                       all warps walking the look-back; tile=1 publishes
+//                       the aggregate before the in-place scans (16-byte
+//                       aligned operands; reverse and row-wise scans need
+//                       segments of a multiple of 4 elements).
 // ept selects V, the 16-byte groups per thread (tile = 256 threads x 4V).
 // float32: element arithmetic is float32; the prefix carried from tile to
 // tile is float64 (one add per tile), rounded to float32 once per tile.
+#include <type_traits>
+
 #include "scan_tile.cuh"
 
 namespace skel {
@@ -246,8 +250,12 @@ scan_tma(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
 constexpr int kBigSub = 4;
 constexpr int kBigTile = kBigSub * kTmaTile;            // 16384 elements
 
-template <class T, bool INCL>
-__global__ void __launch_bounds__(kBlock)
+// EARLY publishes the tile aggregate before the in-place scans (one extra
+// pass over the staged tile) so that successors stop waiting sooner;
+// otherwise the aggregate follows the scans.  Three blocks per SM: the
+// 64 KiB tiles allow three, so registers are capped to keep them.
+template <class T, bool INCL, bool REV, bool EARLY>
+__global__ void __launch_bounds__(kBlock, 3)
 scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc d, Control *ctl, uint32_t epoch,
          int64_t skip_tile, uint64_t limit_ns)
 {
@@ -259,6 +267,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     __shared__ int64_t s_tile;
     __shared__ T smem[kBlock / 32 + 1];
     __shared__ dev::WideLookbackSmem<CT, kBlock / 32> lbs;
+    __shared__ T red[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         const uint32_t t = atomicAdd(&ctl->ticket, 1u);
@@ -268,6 +277,8 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         int64_t first0;
         const TileMap m0 = tile_map<kBigTile>(g, t, &first0);
+        // the tile's physical range: [base, base + len) forward, [base - len + 1, base] reverse
+        const int64_t pstart = m0.rev ? m0.base - (m0.len - 1) : m0.base;
         const uint32_t bytes = (uint32_t)((m0.len * (int64_t)sizeof(T)) & ~(int64_t)15);
         const uint32_t b = smem_u32(&bar);
         if (bytes == 0) {
@@ -277,7 +288,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
             for (uint32_t c = 0; c < bytes; c += 16384u) {
                 const uint32_t sz = bytes - c < 16384u ? bytes - c : 16384u;
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             :: "r"(smem_u32(dyn + c)), "l"(reinterpret_cast<const unsigned char *>(in + m0.base) + c),
+                             :: "r"(smem_u32(dyn + c)), "l"(reinterpret_cast<const unsigned char *>(in + pstart) + c),
                                 "r"(sz), "r"(b)
                              : "memory");
             }
@@ -299,7 +310,79 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
                          : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
         return;   // the tile is never published: its successors' bounded waits give up
     }
-    const int64_t whole = m.len & ~(int64_t)3;
+    // Logical element e (scan order) sits at shared index e forward and
+    // len-1-e reverse.  Reverse tiles have len % 4 == 0 (checked on the host),
+    // so their groups of four are whole 16-byte vectors too.
+    constexpr bool rev = REV;
+    const int64_t len = m.len;
+    const int64_t whole = len & ~(int64_t)3;   // staged elements
+    auto src4 = [&](int64_t e, T (&a)[4]) {    // input values of logical e..e+3
+        if (e + 3 < whole) {
+            if (!rev) {
+                const V4 q = *reinterpret_cast<const V4 *>(buf + e);
+                a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+            } else {
+                const V4 q = *reinterpret_cast<const V4 *>(buf + (len - 4 - e));
+                a[0] = q.w; a[1] = q.z; a[2] = q.y; a[3] = q.x;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)   // the unstaged forward tail is read directly
+                a[i] = e + i < whole ? buf[rev ? len - 1 - e - i : e + i] : (e + i < len ? in[m.base + e + i] : T(0));
+        }
+    };
+    auto put4 = [&](int64_t e, const T (&a)[4]) {   // scanned values back into the same slots
+        if (e + 3 < len) {
+            V4 q;
+            if (!rev) { q.x = a[0]; q.y = a[1]; q.z = a[2]; q.w = a[3]; *reinterpret_cast<V4 *>(buf + e) = q; }
+            else { q.x = a[3]; q.y = a[2]; q.z = a[1]; q.w = a[0]; *reinterpret_cast<V4 *>(buf + (len - 4 - e)) = q; }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (e + i < len) buf[rev ? len - 1 - e - i : e + i] = a[i];
+        }
+    };
+    auto get4 = [&](int64_t e, T (&a)[4]) {         // scanned values of logical e..e+3
+        if (e + 3 < len) {
+            if (!rev) {
+                const V4 q = *reinterpret_cast<const V4 *>(buf + e);
+                a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w;
+            } else {
+                const V4 q = *reinterpret_cast<const V4 *>(buf + (len - 4 - e));
+                a[0] = q.w; a[1] = q.z; a[2] = q.y; a[3] = q.x;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = e + i < len ? buf[rev ? len - 1 - e - i : e + i] : T(0);
+        }
+    };
+    // Early aggregate: pairwise sums of this thread's 16 groups, one sub-tile
+    // at a time (float32 rounding depth 6), then the warp and block trees.
+    // The first tile of a segment publishes its inclusive prefix (= the
+    // aggregate) at once.
+    const bool pub = tile != skip_tile;
+    T tile_agg = T(0);
+    if constexpr (EARLY) {
+        using AddOp = typename std::conditional<std::is_same<T, float>::value, dev::AddF, dev::AddU>::type;
+        T part[kBigSub];
+#pragma unroll
+        for (int j = 0; j < kBigSub; ++j) {
+            T gs[kTmaV];
+#pragma unroll
+            for (int k = 0; k < kTmaV; ++k) {
+                T a[4];
+                src4((int64_t)j * kTmaTile + w * 128 * kTmaV + k * 128 + lane * 4, a);
+                gs[k] = (a[0] + a[1]) + (a[2] + a[3]);
+            }
+            part[j] = (gs[0] + gs[1]) + (gs[2] + gs[3]);
+        }
+        tile_agg = dev::block_reduce<AddOp, T, kBlock>((part[0] + part[1]) + (part[2] + part[3]), red);
+        if (pub && threadIdx.x == 0) {
+            constexpr int W = dev::Codec<CT>::W;
+            if (tile == first) dev::Codec<CT>::put(d.incl + tile * W, (CT)tile_agg, epoch);
+            else dev::Codec<CT>::put(d.agg + tile * W, (CT)tile_agg, epoch);
+        }
+    }
     // pass A: scan every sub-tile in place; carries between sub-tiles in CT
     CT carry[kBigSub];
     CT run = CT(0);
@@ -307,48 +390,34 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     for (int j = 0; j < kBigSub; ++j) {
         carry[j] = run;
         const int64_t off = (int64_t)j * kTmaTile;
-        if (off >= m.len) continue;                          // block-uniform
+        if (off >= len) continue;                            // block-uniform
         T v[kTmaV][4];
 #pragma unroll
-        for (int k = 0; k < kTmaV; ++k) {
-            const int64_t e = off + w * 128 * kTmaV + k * 128 + lane * 4;
-            if (e + 3 < whole) {
-                const V4 q = *reinterpret_cast<const V4 *>(buf + e);
-                v[k][0] = q.x; v[k][1] = q.y; v[k][2] = q.z; v[k][3] = q.w;
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    v[k][i] = e + i < whole ? buf[e + i] : (e + i < m.len ? in[m.base + e + i] : T(0));
-            }
-        }
+        for (int k = 0; k < kTmaV; ++k) src4(off + w * 128 * kTmaV + k * 128 + lane * 4, v[k]);
         const T agg = dev::tile_scan_local<T, INCL, kBlock, kTmaV>(v, smem);
 #pragma unroll
-        for (int k = 0; k < kTmaV; ++k) {
-            const int64_t e = off + w * 128 * kTmaV + k * 128 + lane * 4;   // the same slots this thread read
-            V4 q;
-            q.x = v[k][0]; q.y = v[k][1]; q.z = v[k][2]; q.w = v[k][3];
-            *reinterpret_cast<V4 *>(buf + e) = q;
-        }
+        for (int k = 0; k < kTmaV; ++k) put4(off + w * 128 * kTmaV + k * 128 + lane * 4, v[k]);   // own slots
         run = run + (CT)agg;
     }
-    const CT p = dev::wide_lookback<CT, kBlock / 32>(tile, first, run, d, epoch, ctl, limit_ns, tile != skip_tile, lbs);
+    // EARLY: the aggregate is out already and the walk publishes the
+    // inclusive prefix from that same value, so successors see one
+    // consistent aggregate; otherwise the walk publishes both.
+    const CT p = EARLY ? dev::wide_lookback<CT, kBlock / 32>(tile, first, (CT)tile_agg, d, epoch, ctl, limit_ns,
+                                                             false, pub && tile != first, lbs)
+                       : dev::wide_lookback<CT, kBlock / 32>(tile, first, run, d, epoch, ctl, limit_ns, pub, pub, lbs);
     // pass B: add the prefix and store, sub-tile by sub-tile
 #pragma unroll
     for (int j = 0; j < kBigSub; ++j) {
         const int64_t off = (int64_t)j * kTmaTile;
-        if (off >= m.len) continue;
+        if (off >= len) continue;
         T v[kTmaV][4];
 #pragma unroll
-        for (int k = 0; k < kTmaV; ++k) {
-            const int64_t e = off + w * 128 * kTmaV + k * 128 + lane * 4;
-            const V4 q = *reinterpret_cast<const V4 *>(buf + e);
-            v[k][0] = q.x; v[k][1] = q.y; v[k][2] = q.z; v[k][3] = q.w;
-        }
+        for (int k = 0; k < kTmaV; ++k) get4(off + w * 128 * kTmaV + k * 128 + lane * 4, v[k]);
         dev::tile_add_prefix<T, kTmaV>(v, dev::to_elem<T>(p + carry[j]));
         TileMap ms;
-        ms.base = m.base + off;
-        ms.len = m.len - off < kTmaTile ? m.len - off : kTmaTile;
-        ms.rev = false;
+        ms.rev = rev;
+        ms.base = rev ? m.base - off : m.base + off;
+        ms.len = len - off < kTmaTile ? len - off : kTmaTile;
         ms.vec = ms.len == kTmaTile;
         dev::tile_store<T, kBlock, kTmaV>(out, ms, v);
     }
@@ -516,14 +585,10 @@ int run_scan_tma(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
     if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
     auto kern = scan_tma<T, INCL>;
     const int dyn = kStages * kTmaTile * (int)sizeof(T);
-    static thread_local bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e != cudaSuccess) return fail_cuda(e, "scan tma: shared memory opt-in");
-        attr_set = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return fail_cuda(e, "scan tma: shared memory opt-in");
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, dyn);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kBlock, dyn);
     if (e != cudaSuccess || occ < 1) return fail(SKEL_ERR_UNSUPPORTED, "scan tma: kernel does not fit an SM");
     int64_t grid = (int64_t)device_info().sms * occ;
     if (grid > g.ntiles) grid = g.ntiles;
@@ -543,25 +608,24 @@ int run_scan_big(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     const T *in = static_cast<const T *>(sc.in);
     T *out = static_cast<T *>(sc.out);
-    if (sc.reverse) return fail(SKEL_ERR_UNSUPPORTED, "scan big: forward scans only");
     if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan big: ept must be 4");
     SegGeom g;
     g.seglen = sc.seg > 0 ? sc.seg : sc.n;
     g.tps = ceil_div(g.seglen, kBigTile);
     g.ntiles = g.tps * (sc.n / g.seglen);
-    g.rev = false;
-    if (!aligned16(in) || !aligned16(out) || (sc.seg > 0 && g.seglen % 4))
+    g.rev = sc.reverse;
+    // bulk copies start on 16-byte boundaries: aligned operands, and segments
+    // of a multiple of 4 elements (reverse 1D scans: n % 4 == 0)
+    if (!aligned16(in) || !aligned16(out) || ((sc.seg > 0 || sc.reverse) && g.seglen % 4))
         return fail(SKEL_ERR_UNSUPPORTED, "scan big: 16-byte aligned operands and segments needed");
     g.vec_ok = true;
     if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
-    auto kern = scan_big<T, INCL>;
+    if (c.tile != 0 && c.tile != 1) return fail(SKEL_ERR_INVALID_ARG, "scan big: tile must be 0 or 1 (early aggregate)");
+    auto kern = sc.reverse ? (c.tile ? scan_big<T, INCL, true, true> : scan_big<T, INCL, true, false>)
+                           : (c.tile ? scan_big<T, INCL, false, true> : scan_big<T, INCL, false, false>);
     const int dyn = kBigTile * (int)sizeof(T);
-    static thread_local bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-        if (e != cudaSuccess) return fail_cuda(e, "scan big: shared memory opt-in");
-        attr_set = true;
-    }
+    cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (ea != cudaSuccess) return fail_cuda(ea, "scan big: shared memory opt-in");
     Scratch scr{};
     int rc = get_scratch(s, 0, 2 * (size_t)g.ntiles, &scr);
     if (rc) return rc;

@@ -19,6 +19,10 @@
 //   1 smem_tile   a block stages 2048 + 2r inputs in shared memory; each
 //                 thread computes 8 consecutive outputs from a register
 //                 window of 8 + 2r values.
+//   2 bulk_tile   a block owns 4096 outputs; interior blocks fetch their
+//                 inputs and halos with one cp.async.bulk on an mbarrier,
+//                 each thread computes four 4-output groups from 16-byte
+//                 shared-memory windows (input and output 16-byte aligned).
 // Adjoint (transpose=true): the mirrored stencil w'(di,dj) = w(-di,-dj) with
 // the same boundary for ZERO and PERIODIC.  For CLAMP, taps that the forward
 // pass clamped onto an edge element fold their weight back onto that edge:
@@ -368,6 +372,80 @@ st1_smem(const float *__restrict__ in, float *__restrict__ out, int64_t n, int b
     }
 }
 
+// 1D bulk-copy tile: 4096 outputs per block.  An interior block fetches its
+// 4096 + 2*HP inputs (HP = R rounded up to a multiple of 4, so every piece
+// stays 16-byte aligned) with one cp.async.bulk completing on an mbarrier;
+// the first and last blocks gather through the boundary map instead.  Thread
+// t computes the 4-output groups t, t + 256, t + 512, t + 768, reading each
+// group's 4 + 2*HP window as 16-byte vectors (consecutive threads 16 bytes
+// apart: no bank conflicts).
+constexpr int kBT = 4096;
+
+template <int R>
+__global__ void __launch_bounds__(256)
+st1_bulk(const float *__restrict__ in, float *__restrict__ out, int64_t n, int b, W33 w, Control *ctl)
+{
+    constexpr int HP = (R + 3) / 4 * 4;
+    constexpr int NV = 1 + 2 * HP / 4;                 // 16-byte reads per group window
+    __shared__ __align__(128) float s[kBT + 2 * HP];
+    __shared__ __align__(8) uint64_t bar;
+    const int64_t t0 = (int64_t)blockIdx.x * kBT;
+    const bool interior = t0 - HP >= 0 && t0 + kBT + HP <= n;
+    if (interior) {
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            constexpr uint32_t bytes = (kBT + 2 * HP) * 4;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         :: "r"(smem_addr(&bar)), "r"(bytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_addr(s)), "l"(in + t0 - HP), "r"(bytes), "r"(smem_addr(&bar)) : "memory");
+        }
+        __syncthreads();                               // the barrier is initialised before anyone polls it
+        uint32_t done = 0;
+        for (uint32_t it = 0; it < (1u << 22) && !done; ++it) {
+            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                         : "=r"(done) : "r"(smem_addr(&bar)) : "memory");
+        }
+        if (!__syncthreads_and(done)) {
+            if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+            return;
+        }
+    } else {
+        for (int j = threadIdx.x; j < kBT + 2 * HP; j += 256) {
+            const int64_t k = t0 - HP + j;
+            const int64_t src = k < n + R ? bmap(k, n, b) : -1;
+            s[j] = src < 0 ? 0.f : __ldg(in + src);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < kBT / 1024; ++u) {
+        const int g = threadIdx.x + 256 * u;
+        const int64_t i0 = t0 + 4 * g;
+        if (i0 >= n) break;
+        float win[4 * NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float4 q = *reinterpret_cast<const float4 *>(s + 4 * g + 4 * v);
+            win[4 * v] = q.x; win[4 * v + 1] = q.y; win[4 * v + 2] = q.z; win[4 * v + 3] = q.w;
+        }
+        float o[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k <= 2 * R; ++k) acc = fmaf(w.w[k], win[q + HP - R + k], acc);
+            o[q] = acc;
+        }
+        if (i0 + 4 <= n) {
+            dev::st_stream(reinterpret_cast<float4 *>(out + i0), make_float4(o[0], o[1], o[2], o[3]));
+        } else {
+            for (int q = 0; q < 4 && i0 + q < n; ++q) out[i0 + q] = o[q];
+        }
+    }
+}
+
 // Exact CLAMP adjoint at the two ends of a 1D stencil (overwrites gin[0],
 // gin[n-1]): sums w[k] g[i] over outputs i and taps k with clamp(i+k) == p.
 __global__ void st1_fold_ends(const float *__restrict__ g, float *__restrict__ gin, int64_t n, int r, W33 w)
@@ -483,6 +561,17 @@ int run1d_r(const Choice &c, const float *in, float *out, int64_t n, int b, cons
         launch_kernel(st1_smem<R>, (unsigned)grid, 256, 0, s, in, out, n, b, w);
         return check_launch("mapoverlap1d smem");
     }
+    if (c.variant == 2) {
+        if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u))
+            return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap 1D bulk: input and output must be 16-byte aligned");
+        const int64_t grid = ceil_div(n, kBT);
+        if (grid > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "mapoverlap1d: too long");
+        Scratch scr{};
+        int rc = get_scratch(s, 0, 0, &scr);
+        if (rc) return rc;
+        launch_kernel(st1_bulk<R>, (unsigned)grid, 256, 0, s, in, out, n, b, w, scr.ctl);
+        return check_launch("mapoverlap1d bulk");
+    }
     return fail(SKEL_ERR_INVALID_ARG, "mapoverlap 1D: unknown variant");
 }
 
@@ -499,12 +588,12 @@ int run1d(const Choice &c, int r, const float *in, float *out, int64_t n, int b,
 
 }  // namespace
 
-int stencil_variant_count(int ndim) { return ndim == 1 ? 2 : 4; }
+int stencil_variant_count(int ndim) { return ndim == 1 ? 3 : 4; }
 const char *stencil_variant_name(int ndim, int v)
 {
-    static const char *n1[] = {"direct", "smem_tile"};
+    static const char *n1[] = {"direct", "smem_tile", "bulk_tile"};
     static const char *n2[] = {"direct", "smem_tile", "tma_tile", "column_walk"};
-    if (ndim == 1) return v >= 0 && v < 2 ? n1[v] : "?";
+    if (ndim == 1) return v >= 0 && v < 3 ? n1[v] : "?";
     return v >= 0 && v < 4 ? n2[v] : "?";
 }
 Choice stencil_default(int ndim) { return ndim == 1 ? Choice{1, 256, 8, 0} : Choice{1, 256, 0, 0}; }

@@ -287,18 +287,22 @@ struct WideLookbackSmem {
     CT result;
 };
 
+// pub_agg: publish the aggregate first (false when the caller already has);
+// pub_incl: publish the inclusive prefix at the end (for the segment's first
+// tile: at once, unless the caller already has).
 template <class CT, int NW>
 __device__ __forceinline__ CT wide_lookback(int64_t tile, int64_t first, CT agg, LookbackDesc d, uint32_t epoch,
-                                            Control *ctl, uint64_t limit_ns, bool publish,
+                                            Control *ctl, uint64_t limit_ns, bool pub_agg, bool pub_incl,
                                             WideLookbackSmem<CT, NW> &sm)
 {
     constexpr int W = Codec<CT>::W;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (tile == first) {
-        if (publish && threadIdx.x == 0) Codec<CT>::put(d.incl + tile * W, agg, epoch);
+        if (pub_incl && threadIdx.x == 0) Codec<CT>::put(d.incl + tile * W, agg, epoch);
         return CT(0);
     }
-    if (publish && threadIdx.x == 0) Codec<CT>::put(d.agg + tile * W, agg, epoch);
+    if (pub_agg && threadIdx.x == 0) Codec<CT>::put(d.agg + tile * W, agg, epoch);
+    const bool publish = pub_incl;
     CT excl = CT(0);
     int64_t pred = tile - 1;
     uint64_t t0 = 0;

@@ -315,9 +315,11 @@ Choice select_variant(const Context &ctx, bool *forced)
     if (it != g_table.end()) {
         const Group &g = it->second;
         const int b = bucket_of(ctx.n);
-        if (g.present[b]) return g.e[b];
-        for (int k = b - 1; k >= 0; --k) if (g.present[k]) return g.e[k];   // extrapolate upward
-        for (int k = b + 1; k < kBuckets; ++k) if (g.present[k]) return g.e[k];
+        // an entry with variant -1 records that the built-in default won there
+        auto pick = [&](int k) { return g.e[k].variant < 0 ? builtin_default(ctx.skeleton) : g.e[k]; };
+        if (g.present[b]) return pick(b);
+        for (int k = b - 1; k >= 0; --k) if (g.present[k]) return pick(k);   // extrapolate upward
+        for (int k = b + 1; k < kBuckets; ++k) if (g.present[k]) return pick(k);
     }
     return builtin_default(ctx.skeleton);
 }
@@ -346,7 +348,7 @@ int dispatch_set(int sk, int fn, int dt, int bucket, int radius, int res, const 
 {
     if (sk < 0 || sk >= SKEL_SK_COUNT) return fail(SKEL_ERR_INVALID_ARG, "unknown skeleton");
     if (bucket < 0 || bucket >= kBuckets) return fail(SKEL_ERR_INVALID_ARG, "bucket out of range");
-    if (c.variant < 0) return fail(SKEL_ERR_INVALID_ARG, "variant must be >= 0");
+    if (c.variant < -1) return fail(SKEL_ERR_INVALID_ARG, "variant must be >= 0, or -1 for the built-in default");
     std::lock_guard<std::mutex> lk(g_tab_mu);
     Group &g = g_table[GroupKey{sk, fn, dt, radius, res}];
     g.e[bucket] = c;
@@ -388,7 +390,7 @@ int dispatch_load(const char *path)
         if (k != 10 || (ss >> extra))
             return fail(SKEL_ERR_TABLE, std::string(path) + ":" + std::to_string(lineno) +
                                             ": expected 10 integers");
-        if (v[0] < 0 || v[0] >= SKEL_SK_COUNT || v[3] < 0 || v[3] >= kBuckets || v[6] < 0)
+        if (v[0] < 0 || v[0] >= SKEL_SK_COUNT || v[3] < 0 || v[3] >= kBuckets || v[6] < -1)
             return fail(SKEL_ERR_TABLE, std::string(path) + ":" + std::to_string(lineno) +
                                             ": field out of range");
         Group &g = fresh[GroupKey{v[0], v[1], v[2], v[4], v[5]}];

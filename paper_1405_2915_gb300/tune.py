@@ -29,7 +29,7 @@ import numpy as np
 import torch
 
 from . import (F32, I32, SK, Container, SkelError, skel_batched, skel_force_variant, skel_load_dispatch_table,
-               skel_map, skel_mapoverlap, skel_maparray, skel_mapreduce, skel_reduce, skel_scan)
+               skel_map, skel_mapoverlap, skel_maparray, skel_mapreduce, skel_reduce, skel_scan, skel_scan_bwd)
 from ._lib import FN
 
 L2_FLUSH_BYTES = 512 << 20
@@ -84,6 +84,7 @@ def candidates(sk_name: str):
                 yield (v, 256, e, 0)
         yield (4, 256, 4, 0)
         yield (5, 256, 4, 0)
+        yield (5, 256, 4, 1)
     elif sk_name == "mapoverlap2d":
         yield (0, 256, 0, 0)
         yield (1, 256, 0, 0)
@@ -93,13 +94,15 @@ def candidates(sk_name: str):
     elif sk_name == "mapoverlap1d":
         yield (0, 256, 0, 0)
         yield (1, 256, 8, 0)
+        yield (2, 256, 0, 0)
     elif sk_name == "maparray":
         for v in (0, 1, 2):
             yield (v, 256, 0, 0)
     elif sk_name == "batched":
-        for v in (0, 1, 2):
+        for v in (0, 1, 2, 4):
             for e in (2, 4, 8):
                 yield (v, 256, e, 0)
+        yield (3, 256, 4, 0)
 
 
 class Instance:
@@ -181,6 +184,20 @@ def instances(nmax_log2: int):
         for incl in (True, False):
             out.append(Instance(f"scan {'incl' if incl else 'excl'} {dn}", "scan", 1 if incl else 0, dt, 0, nmax,
                                 mk_scan(dt, incl), lambda n: 8 * n, sizes))
+
+    def mk_rscan(incl):   # the reverse scan of the adjoint (its own keys: fn 3 inclusive, 2 exclusive)
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                bufs["x"], bufs["o"] = vec(nmax), vec(nmax)
+            x, o = Container.from_tensor(bufs["x"][:n]), Container.from_tensor(bufs["o"][:n])
+            return lambda: skel_scan_bwd("add", incl, x, o)
+        return make
+
+    for incl in (True, False):
+        out.append(Instance(f"reverse scan {'incl' if incl else 'excl'} f32", "scan", 3 if incl else 2, F32, 0, nmax,
+                            mk_rscan(incl), lambda n: 8 * n, sizes))
 
     def mk_st2(fn):
         bufs = {}
@@ -289,10 +306,14 @@ def tune(args):
                 skel_force_variant(sk_id, *cand)
                 try:
                     t = timer.time(fn, nb, args.reps)
-                except SkelError:
+                except SkelError as e:
+                    if args.verbose:
+                        print(f"    {inst.name} n={n} {cand}: not applicable ({e})", flush=True)
                     continue
                 finally:
                     skel_force_variant(sk_id, -1)
+                if args.verbose:
+                    print(f"    {inst.name} n={n} {cand}: {nb / t / 1e6:.1f} GB/s", flush=True)
                 if t < t_best:
                     best, t_best = cand, t
             if best is not None and t_best < t_def * (1.0 - args.margin):
@@ -301,6 +322,9 @@ def tune(args):
                 chosen = best
                 t_tuned = t_best
             else:
+                # record that the default won here, so this bucket never
+                # inherits a neighbouring bucket's choice by extrapolation
+                lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 -1 0 0 0")
                 chosen, t_tuned = "default", t_def
             chosen_all.append((inst.name, n, chosen))
             report.append(f"| {inst.name} | {n} | {nb / t_def / 1e6:.1f} | {nb / t_tuned / 1e6:.1f} | "
@@ -323,6 +347,8 @@ def tune(args):
                 best, t_best = cand, t
         if best is not None and t_best < t_def * (1.0 - args.margin):
             lines.append(f"{sk_id} 0 {F32} {bucket(total)} 0 0 {best[0]} {best[1]} {best[2]} {best[3]}")
+        else:
+            lines.append(f"{sk_id} 0 {F32} {bucket(total)} 0 0 -1 0 0 0")
         report.append(f"| batched sumsq+scan f32 | {total} | {nb / t_def / 1e6:.1f} | {nb / t_best / 1e6:.1f} | "
                       f"{t_def / t_best:.3f} | {best if best and t_best < t_def * (1 - args.margin) else 'default'} |")
         print(report[-1], flush=True)
@@ -365,6 +391,7 @@ def main():
     ap.add_argument("--nmax-log2", type=int, default=28)
     ap.add_argument("--only", nargs="*", default=None)
     ap.add_argument("--no-validate", action="store_true")
+    ap.add_argument("--verbose", action="store_true", help="log every candidate's time")
     args = ap.parse_args()
     t0 = time.time()
     report = tune(args)

@@ -140,3 +140,38 @@ def test_composed_loss_8192_fd_and_oracle_gradient():
         fd = (oracle.composed_loss_delta_f32(x, 1, w9, i, j, h) -
               oracle.composed_loss_delta_f32(x, 1, w9, i, j, -h)) / (2 * h)
         assert abs(g[i, j] - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, g[i, j], fd)
+
+
+@pytest.mark.parametrize("n", [4, 4096, 16384, 16388, 1_000_000, 1 << 22])
+@pytest.mark.parametrize("inclusive", [True, False])
+@pytest.mark.parametrize("early", [0, 1])
+def test_scan_bwd_big_tiles(n, inclusive, early):
+    """Reverse scans through the staged big-tile variant (n % 4 == 0)."""
+    import torch
+    from helpers import forced
+    sk = skel()
+    g = syn.uniform_f32(10, n)
+    out = dev_empty((n,), torch.float32)
+    with forced("scan", 5, 0, 0, early):
+        sk.skel_scan_bwd("add", inclusive, wrap(dev_tensor(g)), wrap(out))
+    ref, ab = oracle.scan_bwd_f32(g, inclusive)
+    assert_prefix_close(to_np(out), ref, ab, f"reverse big n={n}")
+
+
+def test_scan_bwd_big_tiles_rows_and_refusal():
+    import torch
+    from helpers import forced
+    sk = skel()
+    rows, cols = 3, 40000
+    g = syn.uniform_f32(11, rows * cols).reshape(rows, cols)
+    out = dev_empty((rows, cols), torch.float32)
+    with forced("scan", 5):
+        sk.skel_scan_bwd("add", True, wrap(dev_tensor(g)), wrap(out))
+        o = to_np(out)
+        for r in range(rows):
+            ref, ab = oracle.scan_bwd_f32(g[r], True)
+            assert_prefix_close(o[r], ref, ab, f"row {r}")
+        bad = dev_empty((4099,), torch.float32)
+        with pytest.raises(sk.SkelError) as e:   # reverse 1D scans need n % 4 == 0 here
+            sk.skel_scan_bwd("add", True, wrap(dev_tensor(syn.uniform_f32(12, 4099))), wrap(bad))
+        assert e.value.code == -4

@@ -59,7 +59,7 @@ def check_batched(v, off, res, scan, inclusive):
         assert_prefix_close(scan, ref, ab, "batched scan")
 
 
-@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8), (2, 4), (1, 8)])
+@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8), (2, 4), (1, 8), (3, 4), (4, 4), (4, 8)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_batched_small_mixed(variant, ept, inclusive):
     """Empty, tiny, unaligned and multi-tile instances mixed."""
@@ -76,9 +76,18 @@ def test_batched_small_mixed(variant, ept, inclusive):
     check_batched(v, off, to_np(res), to_np(sc), inclusive)
 
 
-def test_batched_only_reduce_and_only_scan():
+@pytest.mark.parametrize("variant", [0, 3])
+def test_batched_only_reduce_and_only_scan(variant):
     import torch
     sk = skel()
+    sk.skel_force_variant("batched", variant)
+    try:
+        _only_reduce_only_scan(sk, torch)
+    finally:
+        sk.skel_force_variant("batched", -1)
+
+
+def _only_reduce_only_scan(sk, torch):
     lens, off, v = batched_inputs(300, hi=1 << 16)
     res = torch.zeros(len(lens), device="cuda")
     sc = torch.zeros(int(off[-1]), device="cuda")
@@ -88,12 +97,21 @@ def test_batched_only_reduce_and_only_scan():
     check_batched(v, off, to_np(res), to_np(sc), True)
 
 
-def test_batched_full_workload_and_graph_plan():
+@pytest.mark.parametrize("variant", [0, 3])
+def test_batched_full_workload_and_graph_plan(variant):
     """4096 instances, log-uniform lengths in [64, 2^20] (~4.4e8 elements):
     direct call, captured plan replayed twice, and per-instance calls on a
     sample of instances all agree with the oracle."""
     import torch
     sk = skel()
+    sk.skel_force_variant("batched", variant)
+    try:
+        _full_workload(sk, torch)
+    finally:
+        sk.skel_force_variant("batched", -1)
+
+
+def _full_workload(sk, torch):
     lens, off, v = batched_inputs(4096)
     dv, doff = dev_tensor(v), dev_tensor(off)
     res = torch.zeros(len(lens), device="cuda")

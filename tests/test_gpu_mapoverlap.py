@@ -87,9 +87,9 @@ def test_mapoverlap2d_unaligned_falls_back():
     assert sk.skel_last_variant("mapoverlap2d")[0] in (0,)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("r", [0, 1, 2, 3, 5, 8, 16])
-@pytest.mark.parametrize("n", [1, 2, 7, 33, 2048, 2049, 100_003])
+@pytest.mark.parametrize("n", [1, 2, 7, 33, 2048, 2049, 4096 * 3 + 5, 100_003])
 @pytest.mark.parametrize("boundary", BOUNDS)
 def test_mapoverlap1d(variant, r, n, boundary):
     import torch
@@ -103,6 +103,26 @@ def test_mapoverlap1d(variant, r, n, boundary):
         assert_elem_close(to_np(dout), oracle.mapoverlap1d_f32(x, r, w, boundary), f"1d r={r} n={n}")
         sk.skel_mapoverlap_bwd("stencil1d", r, w, boundary, wrap(dev_tensor(x)), wrap(dout))
     assert_elem_close(to_np(dout), oracle.mapoverlap1d_bwd_f32(x, r, w, boundary), f"1d adjoint r={r} n={n}")
+
+
+def test_mapoverlap1d_bulk_needs_alignment():
+    """The bulk-copy variant refuses a 4-byte-offset input when forced; the
+    dispatched call falls back to a variant without the constraint."""
+    import torch
+    sk = skel()
+    n, r = 50_001, 3
+    x = syn.uniform_f32(96, n + 1)
+    w = syn.uniform_f32(97, 2 * r + 1, 0.0, 1.0)
+    dx = dev_tensor(x)
+    dout = dev_empty((n,), torch.float32)
+    cx = wrap(dx)
+    view = cx.view(1, (n,))
+    with forced("mapoverlap1d", 2):
+        with pytest.raises(sk.SkelError):
+            sk.skel_mapoverlap("stencil1d", r, w, "clamp", view, wrap(dout))
+    sk.skel_mapoverlap("stencil1d", r, w, "clamp", view, wrap(dout))
+    assert_elem_close(to_np(dout), oracle.mapoverlap1d_f32(x[1:], r, w, "clamp"), "offset input")
+    view.close()
 
 
 def test_mapoverlap1d_default_binomial_weights():

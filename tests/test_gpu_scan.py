@@ -11,24 +11,26 @@ from helpers import assert_prefix_close, dev_empty, dev_tensor, forced, skel, to
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
-SCAN_CONFIGS = [(0, 4), (0, 2), (1, 4), (1, 2), (1, 8), (2, 4), (2, 8), (3, 4), (3, 2), (3, 8), (4, 4), (5, 4)]
+# (variant, ept, tile); variant 5 with tile 1 publishes the tile aggregate early
+SCAN_CONFIGS = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (1, 8, 0), (2, 4, 0), (2, 8, 0), (3, 4, 0), (3, 2, 0),
+                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1)]
 
 
 def mod32(a):
     return np.asarray(a, dtype=np.int64).astype(np.int32)
 
 
-@pytest.mark.parametrize("variant,ept", SCAN_CONFIGS)
+@pytest.mark.parametrize("variant,ept,tile", SCAN_CONFIGS)
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("inclusive", [True, False])
 @pytest.mark.parametrize("pad", [0, 1])
-def test_scan_i32_exact(variant, ept, n, inclusive, pad):
+def test_scan_i32_exact(variant, ept, tile, n, inclusive, pad):
     import torch
     sk = skel()
     x = syn.uniform_int(syn.SEED_INT + n, n, 0, 100)
     dx = dev_tensor(x, pad)
     dout = dev_empty((n,), torch.int32, pad)
-    with forced("scan", variant, 0, ept):
+    with forced("scan", variant, 0, ept, tile):
         if variant in (4, 5) and pad % 4:
             # bulk copies need 16-byte aligned operands; a forced call does not fall back
             with pytest.raises(sk.SkelError) as e:
@@ -39,16 +41,16 @@ def test_scan_i32_exact(variant, ept, n, inclusive, pad):
     assert np.array_equal(to_np(dout), mod32(oracle.scan_i32(x, inclusive)))
 
 
-@pytest.mark.parametrize("variant,ept", SCAN_CONFIGS)
+@pytest.mark.parametrize("variant,ept,tile", SCAN_CONFIGS)
 @pytest.mark.parametrize("n", SIZES)
 @pytest.mark.parametrize("inclusive", [True, False])
-def test_scan_f32(variant, ept, n, inclusive):
+def test_scan_f32(variant, ept, tile, n, inclusive):
     import torch
     sk = skel()
     x = syn.uniform_f32(syn.SEED_X + n, n)
     dx = dev_tensor(x)
     dout = dev_empty((n,), torch.float32)
-    with forced("scan", variant, 0, ept):
+    with forced("scan", variant, 0, ept, tile):
         sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
     ref, ab = oracle.scan_f32(x, inclusive)
     assert_prefix_close(to_np(dout), ref, ab, f"scan f32 n={n} incl={inclusive}")
