@@ -408,15 +408,17 @@ def e2e_run(sk, torch, steps, stream):
     one_step()                             # warm-up (allocates device and pinned copies)
     b0 = stats()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    per_step = []
     for _ in range(steps):
+        t0 = time.perf_counter()
         one_step()
-    torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
+        torch.cuda.synchronize()
+        per_step.append(time.perf_counter() - t0)
+    dt = sum(per_step) / steps
     b1 = stats()
     for v in c.values():
         v.close()
-    return dt, (b1[0] - b0[0]) / steps, (b1[1] - b0[1]) / steps, cpus
+    return dt, (b1[0] - b0[0]) / steps, (b1[1] - b0[1]) / steps, cpus, per_step
 
 
 # -------------------------------------------------------------------- main --
@@ -431,6 +433,8 @@ def main():
     ap.add_argument("--only", default=None,
                     help="profiling: comma-separated call names; times only those calls (no default-variant, "
                          "e2e or CPU legs)")
+    ap.add_argument("--force", action="append", default=[], metavar="SKELETON=V[,BLOCK,EPT,TILE]",
+                    help="profiling: force a variant (e.g. scan=5,256,4,0); implies --only semantics for legs")
     ap.add_argument("--n-log2", type=int, default=28, help="profiling: elements per skeleton (even, >= 16)")
     ap.add_argument("--batched-instances", type=int, default=4096, help="profiling: batched instance count")
     args = ap.parse_args()
@@ -463,6 +467,13 @@ def main():
         sk.skel_load_dispatch_table(TABLE)
     wl = Workload(sk, torch, rank)
     calls = wl.calls()
+    for f in args.force:
+        name, _, spec = f.partition("=")
+        try:
+            sk.skel_force_variant(name, *[int(v) for v in spec.split(",")])
+        except (KeyError, ValueError, TypeError):
+            ap.error(f"--force {f}: expected SKELETON=V[,BLOCK,EPT,TILE]")
+        args.no_e2e = args.no_cpu = True
     if args.only:
         keep = set(args.only.split(","))
         calls = [c for c in calls if c[0] in keep]
@@ -494,7 +505,7 @@ def main():
     value = whole_job_gbs(step_bytes, world, args.steps, t_max)
 
     # the fixed default variants (empty table), same steps
-    if args.only:
+    if args.only or args.force:
         def_ms, per_def = total_ms, per
     else:
         sk.skel_load_dispatch_table(None)
@@ -530,11 +541,12 @@ def main():
     del wl, calls
     torch.cuda.empty_cache()
     if not args.no_e2e:
-        dt, h2d, d2h, cpus = e2e_run(sk, torch, min(args.steps, 3), stream)
+        dt, h2d, d2h, cpus, per_step = e2e_run(sk, torch, min(args.steps, 3), stream)
         dt = max_over_ranks(dt * 1e3) / 1e3
         line["e2e"] = {"value": round(world * step_bytes / dt / 1e9, 1), "unit": "GB/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": round(dt * 1e3, 2),
+                       "step_ms": [round(x * 1e3, 1) for x in per_step],
                        "host_cpus": "gpu-local" if cpus else "unchanged"}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()

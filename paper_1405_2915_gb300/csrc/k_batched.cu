@@ -182,14 +182,14 @@ constexpr int kBigTile = kBigSub * kSubTile;            // 16384 elements
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 template <bool SCAN, bool RED, bool INCL>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 3)
 batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ results,
             float *__restrict__ scan_out, Layout L, uint64_t *words, int64_t max_t, int64_t total_elems, Control *ctl,
             uint32_t epoch, uint64_t limit_ns)
 {
     extern __shared__ __align__(1024) unsigned char dyn[];   // kBigTile floats
     float *buf = reinterpret_cast<float *>(dyn);
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[kBigSub];   // one per 16 KiB chunk (= sub-tile)
     __shared__ int64_t s_meta[5];   // tile, instance, lo, hi, first
     __shared__ int64_t s_last;
     __shared__ float smem[kBlock / 32 + 1];
@@ -212,20 +212,23 @@ batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, f
             end = (end + 3) & ~(int64_t)3;                      // whole 16-byte groups ...
             if (end > (total_elems & ~(int64_t)3)) end = total_elems & ~(int64_t)3;   // ... inside the array
             const uint32_t bytes = end > fbase ? (uint32_t)((end - fbase) * 4) : 0u;
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar)) : "memory");
+#pragma unroll
+            for (int c = 0; c < kBigSub; ++c)
+                asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bars[c])) : "memory");
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            const uint32_t bb = smem_u32(&bar);
-            if (bytes == 0) {
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bb) : "memory");
-            } else {
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bb), "r"(bytes) : "memory");
-                for (uint32_t c = 0; c < bytes; c += 16384u) {
-                    const uint32_t sz = bytes - c < 16384u ? bytes - c : 16384u;
-                    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                                 :: "r"(smem_u32(dyn + c)),
-                                    "l"(reinterpret_cast<const unsigned char *>(values + fbase) + c), "r"(sz), "r"(bb)
-                                 : "memory");
+#pragma unroll
+            for (int c = 0; c < kBigSub; ++c) {
+                const uint32_t bb = smem_u32(&bars[c]), o = (uint32_t)c * 16384u;
+                if (o >= bytes) {   // nothing staged in this chunk: complete its phase at once
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(bb) : "memory");
+                    continue;
                 }
+                const uint32_t sz = bytes - o < 16384u ? bytes - o : 16384u;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bb), "r"(sz) : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(smem_u32(dyn + o)),
+                                "l"(reinterpret_cast<const unsigned char *>(values + fbase) + o), "r"(sz), "r"(bb)
+                             : "memory");
             }
         }
     }
@@ -238,17 +241,24 @@ batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, f
     int64_t fend = fbase + kBigTile < hi ? fbase + kBigTile : hi;
     fend = (fend + 3) & ~(int64_t)3;
     if (fend > (total_elems & ~(int64_t)3)) fend = total_elems & ~(int64_t)3;   // staged: [fbase, fend)
-    uint32_t done = 0;
-    for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
-    if (!__syncthreads_and(done)) {
-        if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+    // Bounded wait for chunk c; block-uniform result.  On failure the block
+    // records the timeout, waits (bounded) for every copy still landing in
+    // its shared memory and leaves without publishing.
+    auto wait_chunk = [&](int c) -> bool {
+        uint32_t done = 0;
         for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
             asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                         : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
-        return;
-    }
+                         : "=r"(done) : "r"(smem_u32(&bars[c])) : "memory");
+        if (__syncthreads_and(done)) return true;
+        if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+        for (int cc = 0; cc < kBigSub; ++cc) {
+            uint32_t ok = 0;
+            for (uint32_t k = 0; k < (1u << 22) && !ok; ++k)
+                asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                             : "=r"(ok) : "r"(smem_u32(&bars[cc])) : "memory");
+        }
+        return false;
+    };
     // element e of the frame: staged if fbase + e < fend, else read directly;
     // positions outside [lo, hi) count as 0
     auto at = [&](int64_t e) -> float {
@@ -256,10 +266,13 @@ batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, f
         if (p < lo || p >= hi) return 0.f;
         return p < fend ? buf[e] : values[p];
     };
-    // early aggregates: pairwise per thread, then the block trees
-    float ps[kBigSub * kBigV], pq[kBigSub * kBigV];
+    // early aggregates, each sub-tile as soon as its chunk has landed:
+    // pairwise per thread (rounding depth 6), then the block trees
+    float ps[kBigSub], pq[kBigSub];
 #pragma unroll
     for (int j = 0; j < kBigSub; ++j) {
+        if (!wait_chunk(j)) return;                             // block-uniform
+        float gs[kBigV], gq[kBigV];
 #pragma unroll
         for (int k = 0; k < kBigV; ++k) {
             const int64_t e = (int64_t)j * kSubTile + w * 128 * kBigV + k * 128 + lane * 4;
@@ -271,40 +284,44 @@ batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, f
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = at(e + i);
             }
-            ps[j * kBigV + k] = (a[0] + a[1]) + (a[2] + a[3]);
-            pq[j * kBigV + k] = fmaf(a[0], a[0], a[1] * a[1]) + fmaf(a[2], a[2], a[3] * a[3]);
+            gs[k] = (a[0] + a[1]) + (a[2] + a[3]);
+            gq[k] = fmaf(a[0], a[0], a[1] * a[1]) + fmaf(a[2], a[2], a[3] * a[3]);
         }
+        ps[j] = (gs[0] + gs[1]) + (gs[2] + gs[3]);
+        pq[j] = (gq[0] + gq[1]) + (gq[2] + gq[3]);
     }
-#pragma unroll
-    for (int st = 1; st < kBigSub * kBigV; st *= 2)
-#pragma unroll
-        for (int i = 0; i + st < kBigSub * kBigV; i += 2 * st) {
-            ps[i] = ps[i] + ps[i + st];
-            pq[i] = pq[i] + pq[i + st];
-        }
-    const float agg_s = SCAN ? dev::block_reduce<dev::AddF, float, kBlock>(ps[0], red) : 0.f;
-    const float agg_q = RED ? dev::block_reduce<dev::AddF, float, kBlock>(pq[0], red) : 0.f;
+    const float agg_s = SCAN ? dev::block_reduce<dev::AddF, float, kBlock>((ps[0] + ps[1]) + (ps[2] + ps[3]), red)
+                             : 0.f;
+    const float agg_q = RED ? dev::block_reduce<dev::AddF, float, kBlock>((pq[0] + pq[1]) + (pq[2] + pq[3]), red)
+                            : 0.f;
     const Pair agg((double)agg_s, (double)agg_q);
     const bool multi = first != last;
     if (multi && threadIdx.x == 0) {
         if (t == first) dev::Codec<Pair>::put(d.incl + t * 2, agg, epoch);
         else dev::Codec<Pair>::put(d.agg + t * 2, agg, epoch);
     }
-    // pass A: scan the sub-tiles in place
-    double carry[kBigSub];
+    // pass A: scan the sub-tiles in place.  The carries into the sub-tiles
+    // are block-uniform: kept in shared memory (written before the barriers
+    // of the sub-tile's scan, read after them) rather than in registers.
+    __shared__ double s_carry[kBigSub];
     double run = 0.0;
     if (SCAN) {
 #pragma unroll
         for (int j = 0; j < kBigSub; ++j) {
-            carry[j] = run;
+            if (threadIdx.x == 0) s_carry[j] = run;
             const int64_t o = (int64_t)j * kSubTile;
             if (fbase + o >= hi) continue;                      // block-uniform
             float v[kBigV][4];
 #pragma unroll
             for (int k = 0; k < kBigV; ++k) {
                 const int64_t e = o + w * 128 * kBigV + k * 128 + lane * 4;
+                if (fbase + e >= lo && fbase + e + 3 < hi && fbase + e + 3 < fend) {
+                    const float4 q = *reinterpret_cast<const float4 *>(buf + e);
+                    v[k][0] = q.x; v[k][1] = q.y; v[k][2] = q.z; v[k][3] = q.w;
+                } else {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v[k][i] = at(e + i);
+                    for (int i = 0; i < 4; ++i) v[k][i] = at(e + i);
+                }
             }
             const float sub = dev::tile_scan_local<float, INCL, kBlock, kBigV>(v, smem);
 #pragma unroll
@@ -325,7 +342,7 @@ batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, f
         for (int j = 0; j < kBigSub; ++j) {
             const int64_t o = (int64_t)j * kSubTile;
             if (fbase + o >= hi) continue;
-            const float pre = (float)(p.s + carry[j]);
+            const float pre = (float)(p.s + s_carry[j]);
 #pragma unroll
             for (int k = 0; k < kBigV; ++k) {
                 const int64_t e = o + w * 128 * kBigV + k * 128 + lane * 4;
@@ -349,6 +366,27 @@ batched_big(const float *__restrict__ values, const int64_t *__restrict__ off, f
 // parallel windows after publishing the tile's aggregate early, from a
 // pairwise sum taken right after the load (variants 0 and 1).
 // words: 2 * max_t aggregate words, then 2 * max_t prefix words.
+// Where tile t lives: its instance b = [lo, hi), the instance's first and
+// last tiles, and the 16-byte aligned frame start.  t >= total: no tile.
+struct TileInfo {
+    int64_t t, b, lo, hi, first, last, fbase;
+};
+
+template <int TILE>
+__device__ __forceinline__ TileInfo tile_info(int64_t t, int64_t total, const Layout &L,
+                                              const int64_t *__restrict__ off)
+{
+    TileInfo x{t, 0, 0, 0, 0, 0, 0};
+    if (t >= total) return x;
+    x.b = L.tile_inst[t];
+    x.lo = off[x.b];
+    x.hi = off[x.b + 1];
+    x.first = L.tile_start[x.b];
+    x.last = L.tile_start[x.b + 1] - 1;
+    x.fbase = (x.lo & ~(int64_t)3) + (t - x.first) * TILE;
+    return x;
+}
+
 template <bool SCAN, bool RED, bool INCL, int V, int LB>
 __global__ void __launch_bounds__(kBlock)
 batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ results,
@@ -364,16 +402,17 @@ batched_main(const float *__restrict__ values, const int64_t *__restrict__ off, 
     __shared__ dev::WideLookbackSmem<Pair, kBlock / 32> wls;
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
     const dev::LookbackDesc d{words, words + 2 * max_t};
+    // A block draws its next ticket only when it is ready to work on it: a
+    // ticket held while an earlier one is still processed would not publish
+    // its aggregate in time, and the look-back walks of the tiles after it
+    // would line up behind that block one after the other.
     while (true) {
         if (threadIdx.x == 0) s_tile = (int64_t)atomicAdd(&ctl->queue, 1u);
         __syncthreads();
-        const int64_t t = s_tile;
-        if (t >= total) break;
-        const int64_t b = L.tile_inst[t];
-        const int64_t lo = off[b], hi = off[b + 1];
-        const int64_t first = L.tile_start[b];
-        const int64_t last = L.tile_start[b + 1] - 1;
-        const int64_t fbase = (lo & ~(int64_t)3) + (t - first) * TILE;
+        const TileInfo cur = tile_info<TILE>(s_tile, total, L, off);
+        if (cur.t >= total) break;
+        const int64_t t = cur.t, b = cur.b, lo = cur.lo, hi = cur.hi, first = cur.first, last = cur.last;
+        const int64_t fbase = cur.fbase;
         const bool multi = first != last;   // block-uniform
         float v[V][4];
         load_masked<V>(values, fbase, lo, hi, v);
@@ -532,7 +571,7 @@ const char *batched_variant_name(int v)
                                   "persistent_warp_lookback"};
     return v >= 0 && v < 5 ? names[v] : "?";
 }
-Choice batched_default() { return Choice{4, 256, 4, 0}; }
+Choice batched_default() { return Choice{3, 256, 4, 0}; }
 
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c) { return layout_bytes(b, tile_of(c)); }
 // aggregate and prefix of every tile, two words (scan carry, sum of squares) each

@@ -9,6 +9,8 @@
 //                 per thread; rowdot: one warp per row, 16-byte coalesced
 //                 row loads, warp-shuffle sum.
 //   2 block_row   rowdot only: one block per row, block-tree sum (long rows).
+//   3 split_row   rowdot only: each row split over several blocks (partials
+//                 in scratch, then a fixed-order combine): few, long rows.
 // A is read through the read-only path; it stays in L1/L2 across rows.
 #include "common.cuh"
 
@@ -118,6 +120,62 @@ rowdot_block(const float *__restrict__ A, int64_t m, const float *__restrict__ M
     }
 }
 
+// Split rows: block (s, i) sums the chunk [s*chunk, (s+1)*chunk) of row i
+// into part[i*S + s]; rowdot_combine then adds a row's S partials in a fixed
+// order (lane-strided, then the warp tree), so the result is deterministic.
+// For few long rows, where one warp or block per row leaves the GPU idle.
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+rowdot_split(const float *__restrict__ A, int64_t m, const float *__restrict__ M, float *__restrict__ part,
+             int64_t chunk)
+{
+    __shared__ float smem[32];
+    const int64_t i = blockIdx.y, S = gridDim.x;
+    const int64_t c0 = (int64_t)blockIdx.x * chunk;
+    const int64_t c1 = c0 + chunk < m ? c0 + chunk : m;
+    const float *row = M + i * m;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (VEC) {   // chunk % 4 == 0 and m % 4 == 0: whole 16-byte groups
+        const float4 *r4 = reinterpret_cast<const float4 *>(row);
+        const float4 *A4 = reinterpret_cast<const float4 *>(A);
+        int64_t k = c0 / 4 + threadIdx.x;
+        const int64_t kend = c1 / 4;
+        for (; k + 768 < kend; k += 1024) {   // four 16-byte row loads in flight per thread
+            float4 p[4], ap[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) p[u] = dev::ld_stream(r4 + k + 256 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) ap[u] = __ldg(A4 + k + 256 * u);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a0 = fmaf(ap[u].x, p[u].x, a0); a1 = fmaf(ap[u].y, p[u].y, a1);
+                a2 = fmaf(ap[u].z, p[u].z, a2); a3 = fmaf(ap[u].w, p[u].w, a3);
+            }
+        }
+        for (; k < kend; k += 256) {
+            const float4 p = dev::ld_stream(r4 + k);
+            const float4 ap = __ldg(A4 + k);
+            a0 = fmaf(ap.x, p.x, a0); a1 = fmaf(ap.y, p.y, a1); a2 = fmaf(ap.z, p.z, a2); a3 = fmaf(ap.w, p.w, a3);
+        }
+    } else {
+        for (int64_t k = c0 + threadIdx.x; k < c1; k += 256) a0 = fmaf(__ldg(A + k), row[k], a0);
+    }
+    const float acc = dev::block_reduce<dev::AddF, float, 256>((a0 + a1) + (a2 + a3), smem);
+    if (threadIdx.x == 0) part[i * S + blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(256)
+rowdot_combine(const float *__restrict__ part, int64_t S, float *__restrict__ out, int64_t n)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    float acc = 0.f;
+    for (int64_t k = lane; k < S; k += 32) acc += part[i * S + k];
+    acc = dev::warp_reduce<dev::AddF>(acc);
+    if (lane == 0) out[i] = acc;
+}
+
 int check_launch(const char *what)
 {
     cudaError_t e = cudaPeekAtLastError();
@@ -134,11 +192,11 @@ unsigned grid_for(int64_t work, int block)
 
 }  // namespace
 
-int maparray_variant_count() { return 3; }
+int maparray_variant_count() { return 4; }
 const char *maparray_variant_name(int v)
 {
-    static const char *names[] = {"scalar", "vec4", "block_row"};
-    return v >= 0 && v < 3 ? names[v] : "?";
+    static const char *names[] = {"scalar", "vec4", "block_row", "split_row"};
+    return v >= 0 && v < 4 ? names[v] : "?";
 }
 Choice maparray_default() { return Choice{1, 256, 0, 0}; }
 
@@ -181,6 +239,28 @@ int launch_maparray(const MapArrayLaunch &ma, const Choice &c, cudaStream_t s)
             if (vec) launch_kernel(rowdot_block<true>, (unsigned)g, block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
             else launch_kernel(rowdot_block<false>, (unsigned)g, block, 0, s, ma.A, ma.m, M, ma.out, ma.n);
             return check_launch("rowdot block");
+        }
+        if (c.variant == 3) {
+            // chunks of at least 8192 elements, about 8 blocks per SM in total
+            if (ma.n > 65535) return fail(SKEL_ERR_UNSUPPORTED, "rowdot split: at most 65535 rows");
+            const int64_t target = (int64_t)device_info().sms * 8;
+            int64_t S = ceil_div(target, ma.n);
+            const int64_t smax = ceil_div(ma.m, 8192);
+            if (S > smax) S = smax;
+            if (S < 1) S = 1;
+            const int64_t chunk = ma.m > 0 ? ceil_div(ceil_div(ma.m, S), 1024) * 1024 : 1024;
+            S = ma.m > 0 ? ceil_div(ma.m, chunk) : 1;   // empty rows: one block writes 0
+            Scratch scr{};
+            int rc = get_scratch(s, (size_t)(ma.n * S) * sizeof(float), 0, &scr);
+            if (rc) return rc;
+            float *part = reinterpret_cast<float *>(scr.data);
+            const dim3 g((unsigned)S, (unsigned)ma.n);
+            if (vec) launch_kernel(rowdot_split<true>, g, block, 0, s, ma.A, ma.m, M, part, chunk);
+            else launch_kernel(rowdot_split<false>, g, block, 0, s, ma.A, ma.m, M, part, chunk);
+            rc = check_launch("rowdot split");
+            if (rc) return rc;
+            launch_kernel(rowdot_combine, (unsigned)ceil_div(ma.n, 8), block, 0, s, part, S, ma.out, ma.n);
+            return check_launch("rowdot combine");
         }
         return fail(SKEL_ERR_INVALID_ARG, "rowdot: unknown variant");
     }

@@ -19,8 +19,9 @@
 //   4 lookback_tma      persistent blocks, each with four tiles in flight in
 //                       shared-memory stages filled by bulk copies
 //                       (cp.async.bulk + mbarrier), so HBM reads continue
-//                       while a block waits in its look-back (forward scans,
-//                       16-byte aligned operands).
+//                       while a block waits in its look-back; a tile's
+//                       aggregate is published one iteration before it is
+//                       scanned (forward scans, 16-byte aligned operands).
 //   5 lookback_big      64 KiB tiles staged in shared memory by bulk copies,
 //                       all warps walking the look-back; tile=1 publishes
 //                       the aggregate before the in-place scans (16-byte
@@ -109,12 +110,19 @@ scan_lookback(const T *__restrict__ in, T *__restrict__ out, SegGeom g,
 // ------------------------------------------------ variant 4: TMA pipeline --
 // A persistent block keeps kStages tiles in flight: thread 0 draws tickets in
 // order and starts a bulk copy (cp.async.bulk, completing on the stage's
-// mbarrier) of each drawn tile into a shared-memory stage; the block consumes
-// the stages in ticket order -- reads the tile from shared memory, refills
-// the stage with the next ticket, scans, walks the look-back, stores.  HBM
-// reads continue while the block waits in its look-back.  A block processes
-// its tickets in increasing order and a tile waits only on smaller tickets,
-// so the smallest unfinished tile always progresses.
+// mbarrier) of each drawn tile into a shared-memory stage.  Iteration i
+// works on two tiles: it takes tile i+1 out of its stage into registers,
+// refills that stage with a new ticket and publishes tile i+1's aggregate
+// at once; then it scans tile i (already in registers), walks its
+// look-back, adds the prefix and stores it.
+//
+// Publishing one tile ahead is what keeps the blocks independent.  A block
+// that published a held tile's aggregate only when it came to scan it would
+// make the next tile's look-back wait for the whole of its own previous
+// tile, and that wait would chain through the blocks in ticket order,
+// serialising them.  A block's current tile waits only on smaller tickets,
+// each of which is already aggregated or is some block's current tile, so
+// the smallest unfinished tile always progresses.
 constexpr int kStages = 4;
 constexpr int kTmaV = 4;
 constexpr int kTmaTile = kBlock * 4 * kTmaV;             // 4096 elements = 16 KiB
@@ -124,6 +132,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)_
 __device__ __forceinline__ void mbar_init(uint64_t *bar)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint32_t mbar_try(const uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return done;
 }
 
 // Thread 0: draws the next ticket for stage s and starts its copy.
@@ -155,37 +171,49 @@ scan_tma(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
 {
     using CT = typename ScanTypes<T>::CT;
     using V4 = typename ScanTypes<T>::V4;
+    using AddOp = typename std::conditional<std::is_same<T, float>::value, dev::AddF, dev::AddU>::type;
+    constexpr int W = dev::Codec<CT>::W;
     extern __shared__ __align__(1024) unsigned char bufs[];   // kStages tiles
     __shared__ __align__(8) uint64_t bars[kStages];
     __shared__ int64_t tile_of[kStages];
     __shared__ T smem[kBlock / 32 + 1];
-    __shared__ CT s_prefix;
-    __shared__ int s_bad;
+    __shared__ T red[32];
+    __shared__ dev::WideLookbackSmem<CT, kBlock / 32> lbs;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) mbar_init(bars + s);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_bad = 0;
         for (int s = 0; s < kStages; ++s) tma_issue<T>(in, g, ctl, s, bufs, bars, tile_of);
     }
     __syncthreads();
-    for (uint32_t it = 0;; ++it) {
-        const int s = it % kStages;
-        const uint32_t parity = (it / kStages) & 1u;
-        const int64_t tile = tile_of[s];
-        if (tile >= g.ntiles) break;                          // block-uniform
+
+    // Takes the tile of iteration i out of its stage: bounded wait for the
+    // copy, a striped read into registers (conflict-free 16-byte reads),
+    // the stage refilled with the next ticket, the aggregate published.
+    // Returns false (block-uniform) when the wait ran out: the error is
+    // recorded and the block waits (bounded) for its copies still landing.
+    auto take = [&](uint32_t i, int64_t &tile, T (&v)[kTmaV][4], T &agg) -> bool {
+        const int s = (int)(i % kStages);
+        tile = tile_of[s];
+        if (tile >= g.ntiles) return true;                  // block-uniform
+        uint32_t done = 0;
+        for (uint32_t k = 0; k < (1u << 22) && !done; ++k) done = mbar_try(bars + s, (i / kStages) & 1u);
+        if (!__syncthreads_and(done)) {
+            if (threadIdx.x == 0) {
+                atomicOr(&ctl->error, kErrTimeout);
+                for (uint32_t i2 = i + 1; i2 < i + kStages; ++i2) {
+                    const int s2 = (int)(i2 % kStages);
+                    if (tile_of[s2] >= g.ntiles) continue;
+                    uint32_t ok = 0;
+                    for (uint32_t k = 0; k < (1u << 22) && !ok; ++k) ok = mbar_try(bars + s2, (i2 / kStages) & 1u);
+                }
+            }
+            return false;
+        }
         int64_t first;
         const TileMap m = tile_map<kTmaTile>(g, tile, &first);
-        // wait for the stage's copy (bounded)
-        uint32_t done = 0;
-        for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
-            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                         : "=r"(done) : "r"(smem_u32(bars + s)), "r"(parity) : "memory");
-        if (!done) s_bad = 1;                                 // benign race: every writer stores 1
-        // read the tile in the striped order of tile_scan_local (conflict-free 16-byte reads)
         const T *buf = reinterpret_cast<const T *>(bufs + (size_t)s * kTmaTile * sizeof(T));
         const int64_t whole = m.len & ~(int64_t)3;            // elements delivered by the copy
-        T v[kTmaV][4];
 #pragma unroll
         for (int k = 0; k < kTmaV; ++k) {
             const int e = w * 128 * kTmaV + k * 128 + lane * 4;
@@ -199,33 +227,45 @@ scan_tma(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
             }
         }
         __syncthreads();                                      // the stage is consumed
-        if (s_bad) {                                          // block-uniform after the barrier
-            if (threadIdx.x == 0) {
-                atomicOr(&ctl->error, kErrTimeout);
-                // wait (bounded) for this block's other copies still in flight
-                for (uint32_t i2 = it + 1; i2 < it + kStages; ++i2) {
-                    const int s2 = i2 % kStages;
-                    if (tile_of[s2] >= g.ntiles) continue;
-                    uint32_t ok = 0;
-                    for (uint32_t k = 0; k < (1u << 22) && !ok; ++k)
-                        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-                                     : "=r"(ok) : "r"(smem_u32(bars + s2)), "r"((i2 / kStages) & 1u) : "memory");
-                }
-            }
-            break;
-        }
         if (threadIdx.x == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads before the async refill
             tma_issue<T>(in, g, ctl, s, bufs, bars, tile_of);
         }
-        const T agg = dev::tile_scan_local<T, INCL, kBlock, kTmaV>(v, smem);
-        if (threadIdx.x < 32) {
-            const CT p = dev::lookback<CT>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, tile != skip_tile);
-            if (threadIdx.x == 0) s_prefix = p;
+        // aggregate: pairwise per thread (rounding depth 4), then the block trees
+        T gs[kTmaV];
+#pragma unroll
+        for (int k = 0; k < kTmaV; ++k) gs[k] = (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
+        agg = dev::block_reduce<AddOp, T, kBlock>((gs[0] + gs[1]) + (gs[2] + gs[3]), red);
+        if (threadIdx.x == 0 && tile != skip_tile) {
+            if (tile == first) dev::Codec<CT>::put(d.incl + tile * W, (CT)agg, epoch);
+            else dev::Codec<CT>::put(d.agg + tile * W, (CT)agg, epoch);
         }
-        __syncthreads();
-        dev::tile_add_prefix<T, kTmaV>(v, dev::to_elem<T>(s_prefix));
+        return true;
+    };
+
+    int64_t tile;
+    T v[kTmaV][4];
+    T agg;
+    bool ok = take(0, tile, v, agg);
+    for (uint32_t it = 0; ok && tile < g.ntiles; ++it) {     // block-uniform
+        int64_t tile_n;
+        T vn[kTmaV][4];
+        T agg_n;
+        ok = take(it + 1, tile_n, vn, agg_n);
+        if (!ok) break;
+        int64_t first;
+        const TileMap m = tile_map<kTmaTile>(g, tile, &first);
+        dev::tile_scan_local<T, INCL, kBlock, kTmaV>(v, smem);
+        const CT p = dev::wide_lookback<CT, kBlock / 32>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, false,
+                                                         tile != skip_tile && tile != first, lbs);
+        dev::tile_add_prefix<T, kTmaV>(v, dev::to_elem<T>(p));
         dev::tile_store<T, kBlock, kTmaV>(out, m, v);
+        tile = tile_n;
+        agg = agg_n;
+#pragma unroll
+        for (int k = 0; k < kTmaV; ++k)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[k][j] = vn[k][j];
     }
     // on the normal exit no copy is in flight: tickets are drawn in order, so
     // once a stage holds an invalid ticket every later stage does too
@@ -263,7 +303,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     using V4 = typename ScanTypes<T>::V4;
     extern __shared__ __align__(1024) unsigned char dyn[];   // kBigTile elements
     T *buf = reinterpret_cast<T *>(dyn);
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bars[kBigSub];          // one per 16 KiB chunk
     __shared__ int64_t s_tile;
     __shared__ T smem[kBlock / 32 + 1];
     __shared__ dev::WideLookbackSmem<CT, kBlock / 32> lbs;
@@ -273,43 +313,60 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         const uint32_t t = atomicAdd(&ctl->ticket, 1u);
         if ((int64_t)t == g.ntiles - 1) ctl->ticket = 0u;   // the last ticket: every block has drawn
         s_tile = t;
-        mbar_init(&bar);
+#pragma unroll
+        for (int c = 0; c < kBigSub; ++c) mbar_init(&bars[c]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         int64_t first0;
         const TileMap m0 = tile_map<kBigTile>(g, t, &first0);
         // the tile's physical range: [base, base + len) forward, [base - len + 1, base] reverse
         const int64_t pstart = m0.rev ? m0.base - (m0.len - 1) : m0.base;
         const uint32_t bytes = (uint32_t)((m0.len * (int64_t)sizeof(T)) & ~(int64_t)15);
-        const uint32_t b = smem_u32(&bar);
-        if (bytes == 0) {
-            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
-        } else {
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
-            for (uint32_t c = 0; c < bytes; c += 16384u) {
-                const uint32_t sz = bytes - c < 16384u ? bytes - c : 16384u;
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             :: "r"(smem_u32(dyn + c)), "l"(reinterpret_cast<const unsigned char *>(in + pstart) + c),
-                                "r"(sz), "r"(b)
-                             : "memory");
+#pragma unroll
+        for (int c = 0; c < kBigSub; ++c) {
+            const uint32_t b = smem_u32(&bars[c]), o = (uint32_t)c * 16384u;
+            if (o >= bytes) {   // nothing staged in this chunk: complete its phase at once
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
+                continue;
             }
+            const uint32_t sz = bytes - o < 16384u ? bytes - o : 16384u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(sz) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(dyn + o)), "l"(reinterpret_cast<const unsigned char *>(in + pstart) + o),
+                            "r"(sz), "r"(b)
+                         : "memory");
         }
     }
     __syncthreads();
     const int64_t tile = s_tile;
     int64_t first;
     const TileMap m = tile_map<kBigTile>(g, tile, &first);
-    uint32_t done = 0;
-    for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
-        asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                     : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
-    if (!__syncthreads_and(done)) {
+    // Bounded wait for chunks [c0, c1); block-uniform result.  On failure the
+    // block records the timeout, waits (bounded) for every copy still landing
+    // in its shared memory and leaves; the tile is never published, so its
+    // successors' bounded waits give up too.
+    auto wait_chunks = [&](int c0, int c1) -> bool {
+        uint32_t ok = 1;
+        for (int c = c0; c < c1; ++c) {
+            uint32_t done = 0;
+            for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+                asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                             : "=r"(done) : "r"(smem_u32(&bars[c])) : "memory");
+            ok &= done;
+        }
+        if (__syncthreads_and(ok)) return true;
         if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
-        // wait once more (bounded) for the copy still in flight into this block's shared memory
-        for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
-            asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                         : "=r"(done) : "r"(smem_u32(&bar)) : "memory");
-        return;   // the tile is never published: its successors' bounded waits give up
-    }
+        for (int c = 0; c < kBigSub; ++c) {
+            uint32_t done = 0;
+            for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
+                asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                             : "=r"(done) : "r"(smem_u32(&bars[c])) : "memory");
+        }
+        return false;
+    };
+    // Forward scans start on sub-tile j (its aggregate, or its in-place scan)
+    // as soon as its chunk has landed; reverse scans wait for the whole tile.
+    constexpr bool kProgressive = !REV;
+    if (!kProgressive && !wait_chunks(0, kBigSub)) return;
     // Logical element e (scan order) sits at shared index e forward and
     // len-1-e reverse.  Reverse tiles have len % 4 == 0 (checked on the host),
     // so their groups of four are whole 16-byte vectors too.
@@ -367,6 +424,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         T part[kBigSub];
 #pragma unroll
         for (int j = 0; j < kBigSub; ++j) {
+            if (kProgressive && !wait_chunks(j, j + 1)) return;   // block-uniform
             T gs[kTmaV];
 #pragma unroll
             for (int k = 0; k < kTmaV; ++k) {
@@ -390,7 +448,8 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     for (int j = 0; j < kBigSub; ++j) {
         carry[j] = run;
         const int64_t off = (int64_t)j * kTmaTile;
-        if (off >= len) continue;                            // block-uniform
+        if (kProgressive && !EARLY && !wait_chunks(j, j + 1)) return;   // block-uniform
+        if (off >= len) continue;                                       // block-uniform
         T v[kTmaV][4];
 #pragma unroll
         for (int k = 0; k < kTmaV; ++k) src4(off + w * 128 * kTmaV + k * 128 + lane * 4, v[k]);

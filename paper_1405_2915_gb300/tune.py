@@ -96,7 +96,7 @@ def candidates(sk_name: str):
         yield (1, 256, 8, 0)
         yield (2, 256, 0, 0)
     elif sk_name == "maparray":
-        for v in (0, 1, 2):
+        for v in (0, 1, 2, 3):
             yield (v, 256, 0, 0)
     elif sk_name == "batched":
         for v in (0, 1, 2, 4):
@@ -317,6 +317,17 @@ def tune(args):
                 if t < t_best:
                     best, t_best = cand, t
             if best is not None and t_best < t_def * (1.0 - args.margin):
+                # confirm against noise (tiny calls last a few microseconds):
+                # time both again and keep the candidate only if it still wins
+                t_def2 = timer.time(fn, nb, args.reps)
+                skel_force_variant(sk_id, *best)
+                try:
+                    t_best2 = timer.time(fn, nb, args.reps)
+                finally:
+                    skel_force_variant(sk_id, -1)
+                if not t_best2 < t_def2 * (1.0 - args.margin):
+                    best = None
+            if best is not None and t_best < t_def * (1.0 - args.margin):
                 lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 "
                              f"{best[0]} {best[1]} {best[2]} {best[3]}")
                 chosen = best
@@ -399,7 +410,7 @@ def main():
     if args.report:
         with open(args.report, "w") as f:
             f.write(f"# Tuned vs default variants on {torch.cuda.get_device_name()}\n\n")
-            f.write("Command: `python -m paper_1405_2915_gb300.tune --report " + args.report + "`\n\n")
+            f.write("Command: `python -m paper_1405_2915_gb300.tune " + " ".join(sys.argv[1:]) + "`\n\n")
             f.write("Device time per call, median of %d runs (CUDA events), L2 flushed before each run when the "
                     "operands fit in L2.  GB/s = algorithmic bytes / time.\n\n" % args.reps)
             f.write("\n".join(report) + "\n\n## Sizes between the tuned buckets\n\n" + "\n".join(val) + "\n")

@@ -23,8 +23,9 @@ def test_gather(variant, m, n):
     assert np.array_equal(to_np(dout).astype(np.float64), oracle.gather_f32(A, idx))   # a copy: exact
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
-@pytest.mark.parametrize("n,m", [(1, 1), (3, 5), (37, 64), (1000, 1000), (64, 65536), (4096, 4096), (5, 1 << 20)])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("n,m", [(1, 1), (3, 5), (37, 64), (1000, 1000), (64, 65536), (4096, 4096), (5, 1 << 20),
+                                 (2, 3_000_001), (3, 0)])
 def test_rowdot(variant, n, m):
     import torch
     sk = skel()
