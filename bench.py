@@ -405,7 +405,8 @@ def e2e_run(sk, torch, steps, stream):
         hs = [c[k].stats() for k in c]
         return sum(s["h2d_bytes"] for s in hs), sum(s["d2h_bytes"] for s in hs)
 
-    one_step()                             # warm-up (allocates device and pinned copies)
+    for _ in range(2):                     # warm-up (allocates device and pinned copies)
+        one_step()
     b0 = stats()
     torch.cuda.synchronize()
     per_step = []
@@ -421,6 +422,53 @@ def e2e_run(sk, torch, steps, stream):
     return dt, (b1[0] - b0[0]) / steps, (b1[1] - b0[1]) / steps, cpus, per_step
 
 
+# ------------------------------------------------- Coulombic potential --
+COUL_SIDE, COUL_ATOMS, COUL_H = 4096, 4096, 0.125
+SFU_PER_SM_CLK = 16          # reciprocal square roots per SM per clock (4 per SM sub-partition)
+
+
+def coulomb_leg(sk, torch, stream, clocks, reps: int = 5):
+    """The Coulombic potential grid (MapArray over grid positions), a widening
+    beyond the step: 4096 x 4096 points, 4096 atoms.  Bound by the SFU rate
+    (one reciprocal square root per point-atom pair); reported apart from
+    the step's GB/s."""
+    dev = torch.device("cuda")
+    m, side = COUL_ATOMS, COUL_SIDE
+    a = np.empty((m, 4), np.float32)
+    a[:, 0] = syn.uniform_f32(syn.SEED_X + 11, m, 0.0, 1.0) * np.float32(side * COUL_H)
+    a[:, 1] = syn.uniform_f32(syn.SEED_X + 12, m, 0.0, 1.0) * np.float32(side * COUL_H)
+    a[:, 2] = syn.uniform_f32(syn.SEED_X + 13, m, 0.5, 4.5)
+    a[:, 3] = syn.uniform_f32(syn.SEED_X + 14, m)
+    atoms = sk.Container.from_tensor(torch.from_numpy(a).to(dev))
+    out_t = torch.empty((side, side), dtype=torch.float32, device=dev)
+    out = sk.Container.from_tensor(out_t)
+    call = lambda: sk.skel_maparray_grid("coulomb", atoms, out, (COUL_H, 0.0))
+    for _ in range(2):
+        call()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        call()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    pairs = float(side) * side * m
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = SFU_PER_SM_CLK * sms * mhz * 1e6
+    achieved = pairs / (ms * 1e-3)
+    atoms.close()
+    out.close()
+    return {"metric": "point-atom pairs per second", "value": round(achieved / 1e12, 3), "unit": "Tpairs/s",
+            "ms": round(ms, 3), "config": {"grid": [side, side], "atoms": m, "h": COUL_H},
+            "roofline": {"bound": "alu", "unit": "Tpairs/s", "peak": round(peak / 1e12, 3),
+                         "frac": round(achieved / peak, 3),
+                         "peak_basis": f"{SFU_PER_SM_CLK} rsqrt/clk/SM x {sms} SMs x {mhz:.0f} MHz"},
+            "variant": list(sk.skel_last_variant("maparray"))}
+
+
 # -------------------------------------------------------------------- main --
 def main():
     ap = argparse.ArgumentParser()
@@ -430,6 +478,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-default", action="store_true", help="profiling: skip the default-variant leg")
     ap.add_argument("--only", default=None,
                     help="profiling: comma-separated call names; times only those calls (no default-variant, "
                          "e2e or CPU legs)")
@@ -505,7 +554,7 @@ def main():
     value = whole_job_gbs(step_bytes, world, args.steps, t_max)
 
     # the fixed default variants (empty table), same steps
-    if args.only or args.force:
+    if args.only or args.force or args.no_default:
         def_ms, per_def = total_ms, per
     else:
         sk.skel_load_dispatch_table(None)
@@ -540,8 +589,10 @@ def main():
             "input_gen_s": round(wl.gen_s, 1)}
     del wl, calls
     torch.cuda.empty_cache()
+    if not args.only and not args.force:
+        line["next"] = {"coulomb_grid": coulomb_leg(sk, torch, stream, clocks)}
     if not args.no_e2e:
-        dt, h2d, d2h, cpus, per_step = e2e_run(sk, torch, min(args.steps, 3), stream)
+        dt, h2d, d2h, cpus, per_step = e2e_run(sk, torch, min(args.steps, 5), stream)
         dt = max_over_ranks(dt * 1e3) / 1e3
         line["e2e"] = {"value": round(world * step_bytes / dt / 1e9, 1), "unit": "GB/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),

@@ -92,7 +92,8 @@ typedef enum {
     SKEL_FN_STENCIL9 = 10,/* 2D 3x3 box (mapoverlap), radius 1 */
     SKEL_FN_STENCIL1D = 11,/* 1D weighted window of radius r <= 16 (mapoverlap) */
     SKEL_FN_GATHER = 12,  /* out[i] = A[clamp(idx[i], 0, m-1)] (maparray) */
-    SKEL_FN_ROWDOT = 13   /* out[i] = sum_k A[k] * M[i, k]     (maparray) */
+    SKEL_FN_ROWDOT = 13,  /* out[i] = sum_k A[k] * M[i, k]     (maparray) */
+    SKEL_FN_COULOMB = 14  /* potential of point charges on a grid (maparray over a grid) */
 } skel_fn;
 
 typedef enum {
@@ -116,7 +117,8 @@ typedef enum {
     SKEL_SK_MAPOVERLAP2D = 5,
     SKEL_SK_MAPARRAY = 6,
     SKEL_SK_BATCHED = 7,
-    SKEL_SK_COUNT = 8
+    SKEL_SK_CHAIN2D = 8,   /* a chain of 2D MapOverlap calls (skel_mapoverlap_chain) */
+    SKEL_SK_COUNT = 9
 } skel_skeleton;
 
 /* ------------------------------------------------------------ library --- */
@@ -277,6 +279,23 @@ int skel_scan_noalloc(skel_fn op, int inclusive, skel_dtype dtype, const void *i
 int skel_mapoverlap(skel_fn fn, int radius, const float *weights, int nweights,
                     skel_boundary boundary, skel_handle in, skel_handle out, void *stream);
 
+/* A chain of `steps` 2D MapOverlap calls, each reading the previous one's
+ * output: out = S^steps(in) with S the stencil of skel_mapoverlap (same fn,
+ * weights and boundary; radius 1).  The composition is one call so that its
+ * implementation is chosen for the chain, not call by call (Sec. II: the
+ * global composition problem; Sec. IV: intermediate results stay on the
+ * device).  Variants: per_call (steps single MapOverlap calls, each
+ * dispatched as skel_mapoverlap would be) and time_blocked (tile = steps per
+ * pass, 1..8: a block stages its tile with that many halo cells and applies
+ * the passes' steps in shared memory; CLAMP and ZERO only), which gives the
+ * per-call result bit for bit.  in, tmp and out are 2D F32 of one shape and
+ * pairwise distinct; tmp holds intermediate steps (NULL allowed when steps
+ * == 1 or when a single time-blocked pass covers all steps; a variant that
+ * needs it then refuses and the call falls back).  in is not modified.
+ * steps >= 1.  Enqueued on `stream`. */
+int skel_mapoverlap_chain(skel_fn fn, const float *weights, int nweights, skel_boundary boundary, int steps,
+                          skel_handle in, skel_handle tmp, skel_handle out, void *stream);
+
 /* MapArray: out[i] = f(A, B[i]) with A read whole (random access) and B per
  * element.  The paper does not define MapArray; the reading used is:
  *   GATHER: A 1D F32 of length m >= 1, B 1D I32 of length n,
@@ -284,6 +303,26 @@ int skel_mapoverlap(skel_fn fn, int radius, const float *weights, int nweights,
  *   ROWDOT: A 1D F32 of length m, B 2D F32 of shape (n, m),
  *           out 1D F32 of length n, out[i] = sum_k A[k] * B[i, k]. */
 int skel_maparray(skel_fn fn, skel_handle whole, skel_handle elem, skel_handle out, void *stream);
+
+/* MapArray whose element is its own position on a regular grid: the
+ * Coulombic potential grid that Sec. III runs with SkePU skeletons (Fig. 2).
+ *   fn = COULOMB: whole = atoms, 2D F32 of shape (m, 4), row k = (x_k, y_k,
+ *   z_k, q_k), 16-byte aligned; out = 2D F32 (rows, cols), out[i, j] at the
+ *   point (j*h, i*h, z0):
+ *     out[i, j] = sum_k q_k / sqrt((j*h - x_k)^2 + (i*h - y_k)^2 + (z0 - z_k)^2)
+ *   params = {h, z0} (nparams = 2), h > 0.  A point that coincides with an
+ *   atom gets an infinite term (as the definition does); so does one whose
+ *   squared distance is below 2^-126 (float32 subnormal, flushed to 0).  Each
+ *   term uses the hardware reciprocal square root (PTX rsqrt.approx, relative
+ *   error within 2^-22.9); terms are accumulated with compensation, so
+ *   |out - exact| stays within a few units of 2^-24 * sum_k |q_k| / r_k.
+ *   m = 0 gives zeros.
+ * The library reads the atoms and writes out on the device (lazy copies as
+ * for every skeleton); enqueued on `stream`.  Errors: SKEL_ERR_DTYPE /
+ * SKEL_ERR_SHAPE for other types or shapes, SKEL_ERR_INVALID_ARG for h <= 0,
+ * wrong nparams, a misaligned atom array or out aliasing the atoms. */
+int skel_maparray_grid(skel_fn fn, skel_handle whole, skel_handle out, const double *params, int nparams,
+                       void *stream);
 
 /* Batched instances: B independent float32 instances laid end to end in
  * `values`; instance b is values[offsets[b] .. offsets[b+1]) with offsets an

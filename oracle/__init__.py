@@ -65,6 +65,8 @@ def _load():
                 "oracle_mapoverlap2d_bwd_f32": (None, [vp, i64, i64, i32, vp, i32, vp]),
                 "oracle_gather_f32": (None, [vp, i64, vp, i64, vp]),
                 "oracle_rowdot_f32": (None, [vp, i64, vp, i64, vp, vp]),
+                "oracle_mapoverlap2d_chain_f32": (None, [vp, i64, i64, i32, vp, i32, i32, vp]),
+                "oracle_coulomb_points_f32": (None, [vp, i64, vp, vp, i64, d, d, vp, vp]),
                 "oracle_batched_f32": (None, [vp, vp, i64, i32, vp, vp, vp]),
                 "oracle_composed_loss_f32": (d, [vp, i64, i64, i32, vp, i32, vp]),
                 "oracle_composed_loss_f64": (d, [vp, i64, i64, i32, vp, i32]),
@@ -181,6 +183,16 @@ def mapoverlap2d_f32(x, r: int, w, boundary: str = "clamp") -> np.ndarray:
     return out
 
 
+def mapoverlap2d_chain_f32(x, r: int, w, boundary: str, steps: int) -> np.ndarray:
+    """S^steps(x) for the 2D stencil S of mapoverlap2d_f32, in float64 throughout."""
+    x, w = _f32(x), _f32(w)
+    assert x.ndim == 2 and w.size == (2 * r + 1) ** 2 and steps >= 0
+    out = np.empty(x.shape, dtype=np.float64)
+    _load().oracle_mapoverlap2d_chain_f32(_p(x), x.shape[0], x.shape[1], r, _p(w), BOUNDARY[boundary], int(steps),
+                                          _p(out))
+    return out
+
+
 def mapoverlap1d_bwd_f32(g, r: int, w, boundary: str = "clamp") -> np.ndarray:
     g, w = _f32(g), _f32(w)
     out = np.empty(g.size, dtype=np.float64)
@@ -213,6 +225,27 @@ def rowdot_f32(A, M):
     ab = np.empty(n, dtype=np.float64)
     _load().oracle_rowdot_f32(_p(A), m, _p(M), n, _p(out), _p(ab))
     return out, ab
+
+
+def coulomb_points_f32(atoms, ii, jj, h: float, z0: float):
+    """Potential of the atoms (m x 4 float32: x, y, z, q) at grid points
+    (ii[p], jj[p]) placed at (jj*h, ii*h, z0).  Returns (value, sum |q|/r)."""
+    atoms = _f32(atoms).reshape(-1, 4)
+    ii = np.ascontiguousarray(ii, dtype=np.int64)
+    jj = np.ascontiguousarray(jj, dtype=np.int64)
+    assert ii.shape == jj.shape
+    out = np.empty(ii.size, dtype=np.float64)
+    ab = np.empty(ii.size, dtype=np.float64)
+    _load().oracle_coulomb_points_f32(_p(atoms), atoms.shape[0], _p(ii), _p(jj), ii.size, float(h), float(z0),
+                                      _p(out), _p(ab))
+    return out, ab
+
+
+def coulomb_grid_f32(atoms, rows: int, cols: int, h: float, z0: float):
+    """The whole grid (rows x cols) of coulomb_points_f32."""
+    ii, jj = np.meshgrid(np.arange(rows), np.arange(cols), indexing="ij")
+    v, ab = coulomb_points_f32(atoms, ii.ravel(), jj.ravel(), h, z0)
+    return v.reshape(rows, cols), ab.reshape(rows, cols)
 
 
 # -------------------------------------------------------------- Batched ---

@@ -16,7 +16,9 @@
  *   - Sec. II (related work, Merge): MapReduce, here read as a reduce over a
  *     mapped sequence, r = (+)_i f(x_i, y_i).
  *   - MapArray has no definition in the paper; the reading used is
- *     out[i] = f(A, B[i]) with A read whole (random access) and B per element.
+ *     out[i] = f(A, B[i]) with A read whole (random access) and B per element
+ *     (or, for the Coulombic potential grid of Sec. III, the element's own
+ *     grid position).
  *   - Backward passes are the adjoints of these linear/elementwise maps,
  *     written from their definitions (scatter form), not from the GPU design.
  *
@@ -243,6 +245,37 @@ void oracle_mapoverlap2d_f32(const float *x, int64_t rows, int64_t cols, int r, 
         }
 }
 
+/* A chain of `steps` 2D mapoverlap applications, out = S^steps(x), every
+ * intermediate kept in float64 (the composition of the definition above). */
+void oracle_mapoverlap2d_chain_f32(const float *x, int64_t rows, int64_t cols, int r, const float *w,
+                                   int boundary, int steps, double *out)
+{
+    const int side = 2 * r + 1;
+    const int64_t n = rows * cols;
+    double *cur = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *nxt = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    for (int64_t p = 0; p < n; ++p) cur[p] = (double)x[p];
+    for (int k = 0; k < steps; ++k) {
+        for (int64_t i = 0; i < rows; ++i)
+            for (int64_t j = 0; j < cols; ++j) {
+                double s = 0.0;
+                for (int di = -r; di <= r; ++di) {
+                    int64_t si = bmap(i + di, rows, boundary);
+                    for (int dj = -r; dj <= r; ++dj) {
+                        int64_t sj = bmap(j + dj, cols, boundary);
+                        double v = (si < 0 || sj < 0) ? 0.0 : cur[si * cols + sj];
+                        s += (double)w[(di + r) * side + (dj + r)] * v;
+                    }
+                }
+                nxt[i * cols + j] = s;
+            }
+        double *t = cur; cur = nxt; nxt = t;
+    }
+    for (int64_t p = 0; p < n; ++p) out[p] = cur[p];
+    free(cur);
+    free(nxt);
+}
+
 /* Backward of 1D mapoverlap, by scatter from the forward definition: each
  * forward output i read x[b(i+k)] with weight w[k], so g[i] * w[k] flows back
  * to source index b(i+k).  Clamped taps therefore fold onto the edge. */
@@ -304,6 +337,31 @@ void oracle_rowdot_f32(const float *A, int64_t m, const float *M, int64_t n, dou
         }
         out[i] = s;
         if (abs_out) abs_out[i] = a;
+    }
+}
+
+/* Coulombic potential grid (Sec. III, the application of Fig. 2, written
+ * there as a MapArray over the atoms): grid point (i, j) sits at
+ * (j*h, i*h, z0); atoms[k] = (x, y, z, q) as float32, row-major m x 4.
+ *   out[p] = sum_k q_k / sqrt((x_p - x_k)^2 + (y_p - y_k)^2 + (z0 - z_k)^2)
+ *   abs_out[p] = sum_k |q_k| / r_k
+ * for the npts points (ii[p], jj[p]); float64 throughout (a coinciding atom
+ * gives an infinite term, as the definition does). */
+void oracle_coulomb_points_f32(const float *atoms, int64_t m, const int64_t *ii, const int64_t *jj, int64_t npts,
+                               double h, double z0, double *out, double *abs_out)
+{
+    for (int64_t p = 0; p < npts; ++p) {
+        const double x = (double)jj[p] * h, y = (double)ii[p] * h;
+        double s = 0.0, a = 0.0;
+        for (int64_t k = 0; k < m; ++k) {
+            const double dx = x - (double)atoms[4 * k], dy = y - (double)atoms[4 * k + 1];
+            const double dz = z0 - (double)atoms[4 * k + 2], q = (double)atoms[4 * k + 3];
+            const double r = sqrt(dx * dx + dy * dy + dz * dz);
+            s += q / r;
+            a += fabs(q) / r;
+        }
+        out[p] = s;
+        if (abs_out) abs_out[p] = a;
     }
 }
 

@@ -271,8 +271,23 @@ def skel_mapoverlap(fn, radius: int, weights, boundary, x: Container, out: Conta
                               x.handle, out.handle, _stream(stream)))
 
 
+def skel_mapoverlap_chain(fn, weights, boundary, steps: int, x: Container, tmp, out: Container, stream=None) -> None:
+    """out = S^steps(x) for the 2D stencil S; tmp (a container of x's shape,
+    or None) holds intermediate steps."""
+    w = _weights(weights)
+    check(lib.skel_mapoverlap_chain(_fn(fn), w[0], w[1], BOUNDARY[boundary] if isinstance(boundary, str) else boundary,
+                                    int(steps), x.handle, tmp.handle if tmp is not None else None, out.handle,
+                                    _stream(stream)))
+
+
 def skel_maparray(fn, whole: Container, elem: Container, out: Container, stream=None) -> None:
     check(lib.skel_maparray(_fn(fn), whole.handle, elem.handle, out.handle, _stream(stream)))
+
+
+def skel_maparray_grid(fn, whole: Container, out: Container, params, stream=None) -> None:
+    """MapArray over out's grid positions (fn "coulomb": params = (h, z0))."""
+    p = (C.c_double * len(params))(*params)
+    check(lib.skel_maparray_grid(_fn(fn), whole.handle, out.handle, p, len(params), _stream(stream)))
 
 
 def skel_batched(values: Container, offsets: Container, results: Container | None,

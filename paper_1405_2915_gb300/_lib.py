@@ -17,12 +17,12 @@ F32, I32, I64 = 0, 1, 2
 OK, ERR_INVALID_ARG, ERR_SHAPE, ERR_DTYPE, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_TABLE = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 FN = {"add": 0, "mul": 1, "max": 2, "axpy": 3, "tanh": 4, "sq": 5, "scale": 6, "sub": 7, "copy": 8,
-      "stencil5": 9, "stencil9": 10, "stencil1d": 11, "gather": 12, "rowdot": 13}
+      "stencil5": 9, "stencil9": 10, "stencil1d": 11, "gather": 12, "rowdot": 13, "coulomb": 14}
 BOUNDARY = {"clamp": 0, "zero": 1, "periodic": 2}
 READ, WRITE, READWRITE = 1, 2, 3
 UNIT_HOST, UNIT_DEVICE = 1, 2
 SK = {"map": 0, "reduce": 1, "mapreduce": 2, "scan": 3, "mapoverlap1d": 4, "mapoverlap2d": 5,
-      "maparray": 6, "batched": 7}
+      "maparray": 6, "batched": 7, "chain2d": 8}
 
 vp, i32, i64, dbl, f32p = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_float)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -52,6 +52,8 @@ SIGNATURES = {
     "skel_scan_noalloc": (i32, [i32, i32, i32, vp, vp, i64, vp]),
     "skel_mapoverlap": (i32, [i32, i32, f32p, i32, i32, vp, vp, vp]),
     "skel_maparray": (i32, [i32, vp, vp, vp, vp]),
+    "skel_mapoverlap_chain": (i32, [i32, f32p, i32, i32, i32, vp, vp, vp, vp]),
+    "skel_maparray_grid": (i32, [i32, vp, vp, C.POINTER(dbl), i32, vp]),
     "skel_batched": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp]),
     "skel_batched_plan_create": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp, C.POINTER(vp)]),
     "skel_plan_launch": (i32, [vp, vp]),

@@ -625,6 +625,71 @@ int skel_mapoverlap(skel_fn fn, int radius, const float *weights, int nweights, 
     });
 }
 
+int skel_mapoverlap_chain(skel_fn fn, const float *weights, int nweights, skel_boundary boundary, int steps,
+                          skel_handle in, skel_handle tmp, skel_handle out, void *stream)
+{
+    return guarded([&] {
+        if (!valid_handle(in) || !valid_handle(out) || (tmp && !valid_handle(tmp)))
+            return fail(SKEL_ERR_INVALID_ARG, "bad handle");
+        if (steps < 1) return fail(SKEL_ERR_INVALID_ARG, "mapoverlap chain: steps must be >= 1");
+        if (in->ndim != 2 || (fn != SKEL_FN_STENCIL5 && fn != SKEL_FN_STENCIL9))
+            return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap chain: 2D STENCIL5 or STENCIL9");
+        if (in->dtype != SKEL_F32 || out->dtype != SKEL_F32 || (tmp && tmp->dtype != SKEL_F32))
+            return fail(SKEL_ERR_DTYPE, "mapoverlap chain: float32 only");
+        auto same = [&](skel_handle h) { return h->ndim == 2 && h->shape[0] == in->shape[0] && h->shape[1] == in->shape[1]; };
+        if (!same(out) || (tmp && !same(tmp))) return fail(SKEL_ERR_SHAPE, "mapoverlap chain: shapes differ");
+        if (overlaps(in, out) || (tmp && (overlaps(tmp, in) || overlaps(tmp, out))))
+            return fail(SKEL_ERR_INVALID_ARG, "mapoverlap chain: in, tmp and out must not overlap");
+        if (boundary < SKEL_CLAMP || boundary > SKEL_PERIODIC) return fail(SKEL_ERR_INVALID_ARG, "unknown boundary");
+        if (weights && nweights != 9) return fail(SKEL_ERR_SHAPE, "2D weights: need 9 values (3x3 row-major)");
+        std::vector<float> wbuf;
+        StencilLaunch st{};
+        st.ndim = 2;
+        st.radius = 1;
+        st.boundary = boundary;
+        st.transpose = false;
+        st.rows = in->shape[0];
+        st.cols = in->shape[1];
+        st.taps5 = fn == SKEL_FN_STENCIL5;
+        st.w = weights ? weights : default_weights(fn, 1, wbuf);
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<Operand> ops{{in, SKEL_READ}, {out, SKEL_WRITE}};
+        if (tmp) ops.push_back({tmp, SKEL_WRITE});
+        int res = 0;
+        int rc = acquire_all(ops, s, &res);
+        if (rc) return rc;
+        if (in->n == 0) return (int)SKEL_OK;
+        const float *src = static_cast<const float *>(ops[0].ptr);
+        float *dout = static_cast<float *>(ops[1].ptr);
+        float *dtmp = tmp ? static_cast<float *>(ops[2].ptr) : nullptr;
+        Context ctx{SKEL_SK_CHAIN2D, fn, SKEL_F32, in->n, steps, res};
+        return run_with_fallback(SKEL_SK_CHAIN2D, ctx, [&](const Choice &c) -> int {
+            if (c.variant == 1) {
+                StencilLaunch f = st;
+                f.in = src;
+                f.out = dout;
+                return launch_stencil_chain_fused(f, steps, dtmp, c, s);
+            }
+            if (c.variant != 0) return fail(SKEL_ERR_INVALID_ARG, "mapoverlap chain: unknown variant");
+            if (steps > 1 && !dtmp) return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap chain: per-call steps need tmp");
+            // per call: each step dispatched as a single 2D MapOverlap; the
+            // last step writes out
+            const float *cur = src;
+            for (int k = 0; k < steps; ++k) {
+                StencilLaunch one = st;
+                one.in = cur;
+                one.out = ((steps - 1 - k) % 2 == 0) ? dout : dtmp;
+                Context c1{SKEL_SK_MAPOVERLAP2D, fn, SKEL_F32, in->n, 1, res};
+                int r1 = run_with_fallback(SKEL_SK_MAPOVERLAP2D, c1,
+                                           [&](const Choice &cc) { return launch_stencil(one, cc, s); }, st2_def);
+                if (r1) return r1;
+                cur = one.out;
+            }
+            return (int)SKEL_OK;
+        }, chain_default);
+    });
+}
+
 int skel_maparray(skel_fn fn, skel_handle whole, skel_handle elem, skel_handle out, void *stream)
 {
     return guarded([&] {
@@ -654,6 +719,33 @@ int skel_maparray(skel_fn fn, skel_handle whole, skel_handle elem, skel_handle o
         MapArrayLaunch ma{fn, (const float *)ops[0].ptr, whole->n, ops[1].ptr, (float *)ops[2].ptr, n};
         Context ctx{SKEL_SK_MAPARRAY, fn, SKEL_F32, fn == SKEL_FN_ROWDOT ? whole->n : n, 0, res};
         return run_with_fallback(SKEL_SK_MAPARRAY, ctx, [&](const Choice &c) { return launch_maparray(ma, c, s); }, ma_def);
+    });
+}
+
+int skel_maparray_grid(skel_fn fn, skel_handle whole, skel_handle out, const double *params, int nparams,
+                       void *stream)
+{
+    return guarded([&] {
+        if (!valid_handle(whole) || !valid_handle(out)) return fail(SKEL_ERR_INVALID_ARG, "bad handle");
+        if (fn != SKEL_FN_COULOMB) return fail(SKEL_ERR_UNSUPPORTED, "maparray grid: fn must be COULOMB");
+        if (whole->dtype != SKEL_F32 || out->dtype != SKEL_F32)
+            return fail(SKEL_ERR_DTYPE, "coulomb: atoms and out must be float32");
+        if (whole->ndim != 2 || whole->shape[1] != 4) return fail(SKEL_ERR_SHAPE, "coulomb: atoms must be (m, 4)");
+        if (out->ndim != 2) return fail(SKEL_ERR_SHAPE, "coulomb: out must be 2D");
+        if (!params || nparams != 2 || !(params[0] > 0.0))
+            return fail(SKEL_ERR_INVALID_ARG, "coulomb: params must be {h > 0, z0}");
+        if (overlaps(out, whole)) return fail(SKEL_ERR_INVALID_ARG, "coulomb: output aliases the atoms");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<Operand> ops{{whole, SKEL_READ}, {out, SKEL_WRITE}};
+        int res = 0;
+        int rc = acquire_all(ops, s, &res);
+        if (rc) return rc;
+        if (out->n == 0) return (int)SKEL_OK;
+        CoulombLaunch cl{(const float *)ops[0].ptr, whole->shape[0], (float *)ops[1].ptr, out->shape[0], out->shape[1],
+                         (float)params[0], (float)params[1]};
+        Context ctx{SKEL_SK_MAPARRAY, SKEL_FN_COULOMB, SKEL_F32, out->n, 0, res};
+        return run_with_fallback(SKEL_SK_MAPARRAY, ctx, [&](const Choice &c) { return launch_coulomb(cl, c, s); },
+                                 maparray_default);
     });
 }
 
@@ -1005,6 +1097,7 @@ int skel_variant_count(int skeleton)
     case SKEL_SK_MAPOVERLAP2D: return stencil_variant_count(2);
     case SKEL_SK_MAPARRAY: return maparray_variant_count();
     case SKEL_SK_BATCHED: return batched_variant_count();
+    case SKEL_SK_CHAIN2D: return chain_variant_count();
     default: return 0;
     }
 }
@@ -1019,6 +1112,7 @@ const char *skel_variant_name(int skeleton, int variant)
     case SKEL_SK_MAPOVERLAP2D: return stencil_variant_name(2, variant);
     case SKEL_SK_MAPARRAY: return maparray_variant_name(variant);
     case SKEL_SK_BATCHED: return batched_variant_name(variant);
+    case SKEL_SK_CHAIN2D: return chain_variant_name(variant);
     default: return "?";
     }
 }

@@ -187,9 +187,26 @@ struct StencilLaunch {
     bool transpose;      // adjoint (mirrored weights, clamp folding)
 };
 int launch_stencil(const StencilLaunch &st, const Choice &c, cudaStream_t s);
+// `steps` applications of a 2D forward stencil fused tile-wise, c.tile steps
+// per pass (ping-pong between st.out and tmp, the last pass writes st.out).
+int launch_stencil_chain_fused(const StencilLaunch &st, int steps, float *tmp, const Choice &c, cudaStream_t s);
+int chain_variant_count();
+const char *chain_variant_name(int v);
+Choice chain_default();
 int stencil_variant_count(int ndim);
 const char *stencil_variant_name(int ndim, int v);
 Choice stencil_default(int ndim);
+
+// MapArray over a grid (fn COULOMB): atoms (m x 4 float32: x, y, z, q),
+// out rows x cols, grid position of out[i, j] = (j*h, i*h, z0).
+struct CoulombLaunch {
+    const float *atoms;
+    int64_t m;
+    float *out;
+    int64_t rows, cols;
+    float h, z0;
+};
+int launch_coulomb(const CoulombLaunch &cl, const Choice &c, cudaStream_t s);
 
 struct MapArrayLaunch {
     int fn;              // SKEL_FN_GATHER / SKEL_FN_ROWDOT

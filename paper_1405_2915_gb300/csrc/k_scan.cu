@@ -287,23 +287,22 @@ scan_tma(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
 // look-back is walked by all warps (one window of 32 each per round), and
 // the prefix is added while the tile is stored.  Four times fewer tiles per
 // byte than the 16 KiB tiles means a four times shorter look-back walk.
-constexpr int kBigSub = 4;
-constexpr int kBigTile = kBigSub * kTmaTile;            // 16384 elements
 
 // EARLY publishes the tile aggregate before the in-place scans (one extra
 // pass over the staged tile) so that successors stop waiting sooner;
-// otherwise the aggregate follows the scans.  Three blocks per SM: the
-// 64 KiB tiles allow three, so registers are capped to keep them.
-template <class T, bool INCL, bool REV, bool EARLY>
-__global__ void __launch_bounds__(kBlock, 3)
+// otherwise the aggregate follows the scans.  SUB sub-tiles of 16 KiB per
+// tile: 64 KiB tiles fit three blocks per SM, 48 KiB tiles four, and the
+// registers are capped so that all of them stay resident.
+template <class T, bool INCL, bool REV, bool EARLY, int SUB>
+__global__ void __launch_bounds__(kBlock, SUB == 4 ? 3 : 4)
 scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc d, Control *ctl, uint32_t epoch,
          int64_t skip_tile, uint64_t limit_ns)
 {
     using CT = typename ScanTypes<T>::CT;
     using V4 = typename ScanTypes<T>::V4;
-    extern __shared__ __align__(1024) unsigned char dyn[];   // kBigTile elements
+    extern __shared__ __align__(1024) unsigned char dyn[];   // (SUB * kTmaTile) elements
     T *buf = reinterpret_cast<T *>(dyn);
-    __shared__ __align__(8) uint64_t bars[kBigSub];          // one per 16 KiB chunk
+    __shared__ __align__(8) uint64_t bars[SUB];          // one per 16 KiB chunk
     __shared__ int64_t s_tile;
     __shared__ T smem[kBlock / 32 + 1];
     __shared__ dev::WideLookbackSmem<CT, kBlock / 32> lbs;
@@ -314,15 +313,15 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         if ((int64_t)t == g.ntiles - 1) ctl->ticket = 0u;   // the last ticket: every block has drawn
         s_tile = t;
 #pragma unroll
-        for (int c = 0; c < kBigSub; ++c) mbar_init(&bars[c]);
+        for (int c = 0; c < SUB; ++c) mbar_init(&bars[c]);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         int64_t first0;
-        const TileMap m0 = tile_map<kBigTile>(g, t, &first0);
+        const TileMap m0 = tile_map<SUB * kTmaTile>(g, t, &first0);
         // the tile's physical range: [base, base + len) forward, [base - len + 1, base] reverse
         const int64_t pstart = m0.rev ? m0.base - (m0.len - 1) : m0.base;
         const uint32_t bytes = (uint32_t)((m0.len * (int64_t)sizeof(T)) & ~(int64_t)15);
 #pragma unroll
-        for (int c = 0; c < kBigSub; ++c) {
+        for (int c = 0; c < SUB; ++c) {
             const uint32_t b = smem_u32(&bars[c]), o = (uint32_t)c * 16384u;
             if (o >= bytes) {   // nothing staged in this chunk: complete its phase at once
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
@@ -339,7 +338,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     __syncthreads();
     const int64_t tile = s_tile;
     int64_t first;
-    const TileMap m = tile_map<kBigTile>(g, tile, &first);
+    const TileMap m = tile_map<SUB * kTmaTile>(g, tile, &first);
     // Bounded wait for chunks [c0, c1); block-uniform result.  On failure the
     // block records the timeout, waits (bounded) for every copy still landing
     // in its shared memory and leaves; the tile is never published, so its
@@ -355,7 +354,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         }
         if (__syncthreads_and(ok)) return true;
         if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
-        for (int c = 0; c < kBigSub; ++c) {
+        for (int c = 0; c < SUB; ++c) {
             uint32_t done = 0;
             for (uint32_t k = 0; k < (1u << 22) && !done; ++k)
                 asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
@@ -366,7 +365,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     // Forward scans start on sub-tile j (its aggregate, or its in-place scan)
     // as soon as its chunk has landed; reverse scans wait for the whole tile.
     constexpr bool kProgressive = !REV;
-    if (!kProgressive && !wait_chunks(0, kBigSub)) return;
+    if (!kProgressive && !wait_chunks(0, SUB)) return;
     // Logical element e (scan order) sits at shared index e forward and
     // len-1-e reverse.  Reverse tiles have len % 4 == 0 (checked on the host),
     // so their groups of four are whole 16-byte vectors too.
@@ -421,9 +420,9 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     T tile_agg = T(0);
     if constexpr (EARLY) {
         using AddOp = typename std::conditional<std::is_same<T, float>::value, dev::AddF, dev::AddU>::type;
-        T part[kBigSub];
+        T part[SUB];
 #pragma unroll
-        for (int j = 0; j < kBigSub; ++j) {
+        for (int j = 0; j < SUB; ++j) {
             if (kProgressive && !wait_chunks(j, j + 1)) return;   // block-uniform
             T gs[kTmaV];
 #pragma unroll
@@ -434,7 +433,11 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
             }
             part[j] = (gs[0] + gs[1]) + (gs[2] + gs[3]);
         }
-        tile_agg = dev::block_reduce<AddOp, T, kBlock>((part[0] + part[1]) + (part[2] + part[3]), red);
+#pragma unroll
+        for (int st = 1; st < SUB; st *= 2)
+#pragma unroll
+            for (int i = 0; i + st < SUB; i += 2 * st) part[i] = part[i] + part[i + st];
+        tile_agg = dev::block_reduce<AddOp, T, kBlock>(part[0], red);
         if (pub && threadIdx.x == 0) {
             constexpr int W = dev::Codec<CT>::W;
             if (tile == first) dev::Codec<CT>::put(d.incl + tile * W, (CT)tile_agg, epoch);
@@ -442,10 +445,10 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         }
     }
     // pass A: scan every sub-tile in place; carries between sub-tiles in CT
-    CT carry[kBigSub];
+    CT carry[SUB];
     CT run = CT(0);
 #pragma unroll
-    for (int j = 0; j < kBigSub; ++j) {
+    for (int j = 0; j < SUB; ++j) {
         carry[j] = run;
         const int64_t off = (int64_t)j * kTmaTile;
         if (kProgressive && !EARLY && !wait_chunks(j, j + 1)) return;   // block-uniform
@@ -466,7 +469,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
                        : dev::wide_lookback<CT, kBlock / 32>(tile, first, run, d, epoch, ctl, limit_ns, pub, pub, lbs);
     // pass B: add the prefix and store, sub-tile by sub-tile
 #pragma unroll
-    for (int j = 0; j < kBigSub; ++j) {
+    for (int j = 0; j < SUB; ++j) {
         const int64_t off = (int64_t)j * kTmaTile;
         if (off >= len) continue;
         T v[kTmaV][4];
@@ -662,27 +665,21 @@ int run_scan_tma(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan tma launch");
 }
 
-template <class T, bool INCL>
-int run_scan_big(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+template <class T, bool INCL, bool REV, int SUB>
+int launch_scan_big(const ScanLaunch &sc, bool early, cudaStream_t s)
 {
     const T *in = static_cast<const T *>(sc.in);
     T *out = static_cast<T *>(sc.out);
-    if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan big: ept must be 4");
+    constexpr int TILE = SUB * kTmaTile;
     SegGeom g;
     g.seglen = sc.seg > 0 ? sc.seg : sc.n;
-    g.tps = ceil_div(g.seglen, kBigTile);
+    g.tps = ceil_div(g.seglen, TILE);
     g.ntiles = g.tps * (sc.n / g.seglen);
-    g.rev = sc.reverse;
-    // bulk copies start on 16-byte boundaries: aligned operands, and segments
-    // of a multiple of 4 elements (reverse 1D scans: n % 4 == 0)
-    if (!aligned16(in) || !aligned16(out) || ((sc.seg > 0 || sc.reverse) && g.seglen % 4))
-        return fail(SKEL_ERR_UNSUPPORTED, "scan big: 16-byte aligned operands and segments needed");
+    g.rev = REV;
     g.vec_ok = true;
     if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
-    if (c.tile != 0 && c.tile != 1) return fail(SKEL_ERR_INVALID_ARG, "scan big: tile must be 0 or 1 (early aggregate)");
-    auto kern = sc.reverse ? (c.tile ? scan_big<T, INCL, true, true> : scan_big<T, INCL, true, false>)
-                           : (c.tile ? scan_big<T, INCL, false, true> : scan_big<T, INCL, false, false>);
-    const int dyn = kBigTile * (int)sizeof(T);
+    auto kern = early ? scan_big<T, INCL, REV, true, SUB> : scan_big<T, INCL, REV, false, SUB>;
+    const int dyn = TILE * (int)sizeof(T);
     cudaError_t ea = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (ea != cudaSuccess) return fail_cuda(ea, "scan big: shared memory opt-in");
     Scratch scr{};
@@ -694,6 +691,24 @@ int run_scan_big(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
                   k.scan_skip_publish_tile, k.wait_limit_ns);
     cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan big launch");
+}
+
+// tile: bit 0 publishes the aggregate early; bit 1 selects 48 KiB tiles
+// (three sub-tiles) instead of 64 KiB ones.
+template <class T, bool INCL>
+int run_scan_big(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+{
+    if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan big: ept must be 4");
+    if (c.tile < 0 || c.tile > 3) return fail(SKEL_ERR_INVALID_ARG, "scan big: tile must be 0..3");
+    // bulk copies start on 16-byte boundaries: aligned operands, and segments
+    // of a multiple of 4 elements (reverse 1D scans: n % 4 == 0)
+    const int64_t seglen = sc.seg > 0 ? sc.seg : sc.n;
+    if (!aligned16(sc.in) || !aligned16(sc.out) || ((sc.seg > 0 || sc.reverse) && seglen % 4))
+        return fail(SKEL_ERR_UNSUPPORTED, "scan big: 16-byte aligned operands and segments needed");
+    const bool early = c.tile & 1, sub3 = c.tile & 2;
+    if (sc.reverse)
+        return sub3 ? launch_scan_big<T, INCL, true, 3>(sc, early, s) : launch_scan_big<T, INCL, true, 4>(sc, early, s);
+    return sub3 ? launch_scan_big<T, INCL, false, 3>(sc, early, s) : launch_scan_big<T, INCL, false, 4>(sc, early, s);
 }
 
 template <class T, bool INCL>

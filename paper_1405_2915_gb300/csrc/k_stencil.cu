@@ -575,6 +575,184 @@ int run1d_r(const Choice &c, const float *in, float *out, int64_t n, int b, cons
     return fail(SKEL_ERR_INVALID_ARG, "mapoverlap 1D: unknown variant");
 }
 
+// ------------------------------------------- 2D chains, time-blocked --
+// K steps of the same 2D stencil fused into one pass (temporal blocking): a
+// block stages its 128 x 32 output tile with a halo of K rows and
+// roundup4(K) + 4 columns, runs the K steps in shared memory (ping-pong
+// between two buffers, the valid area shrinking by one cell per step) and
+// writes only the tile.  HBM traffic drops K-fold against K separate calls.
+//
+// Boundaries: staged cells outside the grid hold what the single-step
+// kernels read there: the clamped neighbour (CLAMP) or 0 (ZERO), re-derived
+// after every step from that step's values (the clamped cell of a border
+// tile always lies in its computed area).  PERIODIC would need cells of the
+// far side of the grid and is not offered.  Each cell is evaluated by
+// stencil9 with the taps in the single-step kernels' order, so K fused steps
+// give bit-for-bit the result of K single calls.
+template <int K>
+struct ChainGeom {
+    // column halo: K rounded up to 16 bytes, plus one group of 4 so that the
+    // 4-column groups computed each step never read outside the staging
+    static constexpr int HL = (K + 3) / 4 * 4 + 4;
+    static constexpr int SW = kTX + 2 * HL;         // staged width
+    static constexpr int SH = kTY + 2 * K;          // staged height
+    static constexpr int NG = SW / 4 - 2;           // 4-column groups computed per row (34 or 36)
+    static constexpr int SR = (SH - 2 + 6) / 7;     // rows per strip: at most 7 strips, so that
+    static constexpr int NS = (SH - 2 + SR - 1) / SR;   // NG * NS <= 256 items, one per thread
+    static_assert(NG * NS <= 256, "one item per thread");
+    static constexpr int smem_bytes = 2 * SH * SW * 4;
+};
+
+template <bool TAPS5, int K>
+__global__ void __launch_bounds__(256)
+st2_chain(const float *__restrict__ in, float *__restrict__ out, int64_t rows, int64_t cols, int b, W9 w)
+{
+    using G = ChainGeom<K>;
+    extern __shared__ __align__(16) float sm[];
+    float *A = sm, *B = sm + G::SH * G::SW;
+    const int64_t tx0 = (int64_t)blockIdx.x * kTX, ty0 = (int64_t)blockIdx.y * kTY;
+    const int64_t gr0 = ty0 - K, gc0 = tx0 - G::HL;          // global position of staged (0, 0)
+    const bool vec = (cols & 3) == 0;
+    const int lane = threadIdx.x & 31;
+    // stage: groups of 4 columns; a group is wholly inside or outside the
+    // grid's columns when cols % 4 == 0 (then one 16-byte load)
+    for (int g = threadIdx.x; g < G::SH * (G::SW / 4); g += 256) {
+        const int sr = g / (G::SW / 4), sc = 4 * (g % (G::SW / 4));
+        const int64_t r = bmap(gr0 + sr, rows, b), c = gc0 + sc;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (r >= 0) {
+            if (vec && c >= 0 && c + 3 < cols) {
+                v = dev::ld_stream(reinterpret_cast<const float4 *>(in + r * cols + c));
+            } else {
+                float *vp = &v.x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int64_t cc = bmap(c + j, cols, b);
+                    vp[j] = cc < 0 ? 0.f : __ldg(in + r * cols + cc);
+                }
+            }
+        }
+        *reinterpret_cast<float4 *>(A + sr * G::SW + sc) = v;
+    }
+    __syncthreads();
+    const bool border = gr0 < 0 || gc0 < 0 || gr0 + G::SH > rows || gc0 + G::SW > cols;   // block-uniform
+#pragma unroll 1
+    for (int step = 0; step < K; ++step) {
+        // B = stencil(A) on rows 1 .. SH-2 and columns 4 .. SW-5.  An item is
+        // one group of 4 columns over a strip of SR rows, walked with a
+        // 3-row register window: one 16-byte read per row, the outer
+        // neighbours from the adjacent lanes (shared memory at warp edges);
+        // four independent tap chains per row.
+        for (int base = 0; base < G::NG * G::NS; base += 256) {   // block-uniform trip count
+            const int item = base + threadIdx.x;
+            const bool live = item < G::NG * G::NS;
+            const int gcol = 4 * (1 + (live ? item % G::NG : 0));
+            const int r0 = 1 + (live ? item / G::NG : 0) * G::SR;
+            const int r1 = r0 + G::SR < G::SH - 1 ? r0 + G::SR : G::SH - 1;
+            // lanes whose left / right group is another lane's: shuffles need
+            // the same item row and adjacent groups
+            const int nrow = live ? item / G::NG : -1;
+            const int lrow = __shfl_up_sync(0xffffffffu, nrow, 1);
+            const int rrow = __shfl_down_sync(0xffffffffu, nrow, 1);
+            const bool lsh = lane > 0 && lrow == nrow && gcol > 4;
+            const bool rsh = lane < 31 && rrow == nrow && gcol < 4 * G::NG;
+            // a row of the window: columns gcol-1 .. gcol+4
+            auto load_row = [&](int sr, float (&v)[6]) {
+                const float *p = A + sr * G::SW + gcol;
+                const float4 q = *reinterpret_cast<const float4 *>(p);
+                const float l = __shfl_up_sync(0xffffffffu, q.w, 1);
+                const float r = __shfl_down_sync(0xffffffffu, q.x, 1);
+                v[0] = lsh ? l : p[-1];
+                v[1] = q.x; v[2] = q.y; v[3] = q.z; v[4] = q.w;
+                v[5] = rsh ? r : p[4];
+            };
+            // every lane runs SR rows (fully unrolled, so the window rotates
+            // by renaming, and the shuffles see all lanes); rows past the
+            // strip's end read a clamped row and are not stored
+            const int rows_here = live ? r1 - r0 : 0;
+            const int rr0 = live ? r0 : 1;
+            float rows_buf[G::SR + 2][6];
+            load_row(rr0 - 1, rows_buf[0]);
+            load_row(rr0, rows_buf[1]);
+#pragma unroll
+            for (int k = 0; k < G::SR; ++k) {
+                const int r = rr0 + k;
+                load_row(r + 1 < G::SH ? r + 1 : G::SH - 1, rows_buf[k + 2]);
+                float4 o;
+                float *op = &o.x;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    op[j] = stencil9<TAPS5>(w, rows_buf[k][j], rows_buf[k][j + 1], rows_buf[k][j + 2],
+                                            rows_buf[k + 1][j], rows_buf[k + 1][j + 1], rows_buf[k + 1][j + 2],
+                                            rows_buf[k + 2][j], rows_buf[k + 2][j + 1], rows_buf[k + 2][j + 2]);
+                if (k < rows_here) *reinterpret_cast<float4 *>(B + r * G::SW + gcol) = o;
+            }
+        }
+        __syncthreads();
+        if (border) {
+            // cells outside the grid take this step's clamped neighbour, or 0
+            constexpr int NC = G::SW - 8;
+            for (int i = threadIdx.x; i < (G::SH - 2) * NC; i += 256) {
+                const int sr = 1 + i / NC, sc = 4 + i % NC;
+                const int64_t r = gr0 + sr, c = gc0 + sc;
+                if (r >= 0 && r < rows && c >= 0 && c < cols) continue;
+                float v = 0.f;
+                if (b == SKEL_CLAMP) {
+                    const int64_t rr = r < 0 ? 0 : (r >= rows ? rows - 1 : r);
+                    const int64_t cc = c < 0 ? 0 : (c >= cols ? cols - 1 : c);
+                    v = B[(rr - gr0) * G::SW + (cc - gc0)];
+                }
+                B[sr * G::SW + sc] = v;
+            }
+            __syncthreads();
+        }
+        float *t = A; A = B; B = t;
+    }
+    // the tile: staged rows K .. K+kTY-1, columns HL .. HL+kTX-1
+    for (int g = threadIdx.x; g < kTY * (kTX / 4); g += 256) {
+        const int tr = g / (kTX / 4), tc = 4 * (g % (kTX / 4));
+        const int64_t r = ty0 + tr, c = tx0 + tc;
+        if (r >= rows) continue;
+        const float *src = A + (K + tr) * G::SW + G::HL + tc;
+        if (vec && c + 3 < cols) {
+            dev::st_stream(reinterpret_cast<float4 *>(out + r * cols + c), *reinterpret_cast<const float4 *>(src));
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c + j < cols) out[r * cols + c + j] = src[j];
+        }
+    }
+}
+
+template <bool TAPS5, int K>
+int run_chain_k(const float *in, float *out, int64_t rows, int64_t cols, int b, const W9 &w, cudaStream_t s)
+{
+    auto kern = st2_chain<TAPS5, K>;
+    constexpr int smem = ChainGeom<K>::smem_bytes;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return fail_cuda(e, "mapoverlap chain: shared memory opt-in");
+    const int64_t gx = ceil_div(cols, kTX), gy = ceil_div(rows, kTY);
+    if (gy > 65535 || gx > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "mapoverlap chain: grid too large");
+    launch_kernel(kern, dim3((unsigned)gx, (unsigned)gy), 256, (size_t)smem, s, in, out, rows, cols, b, w);
+    return check_launch("mapoverlap chain");
+}
+
+template <bool TAPS5>
+int run_chain(int k, const float *in, float *out, int64_t rows, int64_t cols, int b, const W9 &w, cudaStream_t s)
+{
+    switch (k) {
+    case 1: return run_chain_k<TAPS5, 1>(in, out, rows, cols, b, w, s);
+    case 2: return run_chain_k<TAPS5, 2>(in, out, rows, cols, b, w, s);
+    case 3: return run_chain_k<TAPS5, 3>(in, out, rows, cols, b, w, s);
+    case 4: return run_chain_k<TAPS5, 4>(in, out, rows, cols, b, w, s);
+    case 5: return run_chain_k<TAPS5, 5>(in, out, rows, cols, b, w, s);
+    case 6: return run_chain_k<TAPS5, 6>(in, out, rows, cols, b, w, s);
+    case 7: return run_chain_k<TAPS5, 7>(in, out, rows, cols, b, w, s);
+    case 8: return run_chain_k<TAPS5, 8>(in, out, rows, cols, b, w, s);
+    default: return fail(SKEL_ERR_INVALID_ARG, "mapoverlap chain: steps per pass must be 1..8");
+    }
+}
+
 int run1d(const Choice &c, int r, const float *in, float *out, int64_t n, int b, const W33 &w, cudaStream_t s)
 {
     switch (r) {
@@ -628,6 +806,37 @@ int launch_stencil(const StencilLaunch &st, const Choice &c, cudaStream_t s)
     if (rc || !st.transpose || st.boundary != SKEL_CLAMP || r == 0) return rc;
     launch_kernel(st1_fold_ends, 1, 32, 0, s, st.in, st.out, st.cols, r, w);
     return check_launch("mapoverlap1d adjoint ends");
+}
+
+int chain_variant_count() { return 2; }
+const char *chain_variant_name(int v)
+{
+    static const char *names[] = {"per_call", "time_blocked"};
+    return v >= 0 && v < 2 ? names[v] : "?";
+}
+Choice chain_default() { return Choice{1, 256, 0, 4}; }
+
+int launch_stencil_chain_fused(const StencilLaunch &st, int steps, float *tmp, const Choice &c, cudaStream_t s)
+{
+    if (st.ndim != 2 || st.transpose) return fail(SKEL_ERR_INVALID_ARG, "mapoverlap chain: 2D forward stencils only");
+    if (st.boundary == SKEL_PERIODIC) return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap chain: periodic is not time-blocked");
+    const int k = c.tile > 0 ? c.tile : 4;
+    if (k < 1 || k > 8) return fail(SKEL_ERR_INVALID_ARG, "mapoverlap chain: tile (steps per pass) must be 1..8");
+    const int passes = (steps + k - 1) / k;
+    if (passes > 1 && !tmp) return fail(SKEL_ERR_UNSUPPORTED, "mapoverlap chain: several passes need tmp");
+    W9 w;
+    for (int q = 0; q < 9; ++q) w.w[q] = st.w[q];
+    if (st.taps5) w.w[0] = w.w[2] = w.w[6] = w.w[8] = 0.f;
+    const float *src = st.in;
+    for (int p = 0; p < passes; ++p) {
+        const int kp = p < passes - 1 ? k : steps - k * (passes - 1);
+        float *dst = ((passes - 1 - p) % 2 == 0) ? st.out : tmp;   // the last pass writes out
+        int rc = st.taps5 ? run_chain<true>(kp, src, dst, st.rows, st.cols, st.boundary, w, s)
+                          : run_chain<false>(kp, src, dst, st.rows, st.cols, st.boundary, w, s);
+        if (rc) return rc;
+        src = dst;
+    }
+    return SKEL_OK;
 }
 
 }  // namespace skel

@@ -142,17 +142,17 @@ def test_composed_loss_8192_fd_and_oracle_gradient():
         assert abs(g[i, j] - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, g[i, j], fd)
 
 
-@pytest.mark.parametrize("n", [4, 4096, 16384, 16388, 1_000_000, 1 << 22])
+@pytest.mark.parametrize("n", [4, 4096, 12288, 12292, 16384, 16388, 1_000_000, 1 << 22])
 @pytest.mark.parametrize("inclusive", [True, False])
-@pytest.mark.parametrize("early", [0, 1])
-def test_scan_bwd_big_tiles(n, inclusive, early):
+@pytest.mark.parametrize("tile", [0, 1, 3])
+def test_scan_bwd_big_tiles(n, inclusive, tile):
     """Reverse scans through the staged big-tile variant (n % 4 == 0)."""
     import torch
     from helpers import forced
     sk = skel()
     g = syn.uniform_f32(10, n)
     out = dev_empty((n,), torch.float32)
-    with forced("scan", 5, 0, 0, early):
+    with forced("scan", 5, 0, 0, tile):
         sk.skel_scan_bwd("add", inclusive, wrap(dev_tensor(g)), wrap(out))
     ref, ab = oracle.scan_bwd_f32(g, inclusive)
     assert_prefix_close(to_np(out), ref, ab, f"reverse big n={n}")

@@ -149,3 +149,64 @@ def test_mapoverlap_rejects_aliasing_and_bad_radius():
     v = torch.zeros(100, device="cuda")
     with pytest.raises(sk.SkelError):
         sk.skel_mapoverlap("stencil1d", 17, None, "clamp", wrap(v), wrap(torch.zeros(100, device="cuda")))
+
+
+# ------------------------------------------------ chains of 2D calls --
+CHAIN_CASES = [((1, 1), 3), ((5, 7), 2), ((33, 130), 5), ((130, 257), 10), ((300, 520), 4), ((64, 128), 1)]
+
+
+def run_chain(sk, kind, boundary, steps, x, with_tmp=True):
+    import torch
+    out = dev_empty(x.shape, torch.float32)
+    tmp = wrap(dev_empty(x.shape, torch.float32)) if with_tmp else None
+    sk.skel_mapoverlap_chain(kind, None, boundary, steps, wrap(dev_tensor(x)), tmp, wrap(out))
+    return to_np(out)
+
+
+@pytest.mark.parametrize("variant,k", [(0, 0), (1, 1), (1, 2), (1, 4), (1, 8)])
+@pytest.mark.parametrize("shape,steps", CHAIN_CASES)
+@pytest.mark.parametrize("kind", ["stencil5", "stencil9"])
+@pytest.mark.parametrize("boundary", ["clamp", "zero"])
+def test_mapoverlap_chain_matches_oracle(variant, k, shape, steps, kind, boundary):
+    """out = S^steps(x) against the float64 chain; each step adds at most a
+    few float32 roundings of values <= 1 (the stencils average)."""
+    sk = skel()
+    x = syn.uniform_f32(syn.SEED_GRID + steps, shape[0] * shape[1], 0.0, 1.0).reshape(shape)
+    with forced("chain2d", variant, 0, 0, k):
+        g = run_chain(sk, kind, boundary, steps, x)
+    w = oracle.stencil_weights("5pt" if kind == "stencil5" else "9pt")
+    ref = oracle.mapoverlap2d_chain_f32(x, 1, w, boundary, steps)
+    assert_elem_close(g, ref, f"chain {kind} {boundary} {shape} x{steps} v{variant} k{k}", atol=1e-6 * steps)
+
+
+@pytest.mark.parametrize("k", [1, 3, 4, 8])
+@pytest.mark.parametrize("boundary", ["clamp", "zero"])
+def test_mapoverlap_chain_time_blocked_is_bitwise_per_call(k, boundary):
+    """The fused passes evaluate every cell with the single-step tap order:
+    the result equals the chain of single calls bit for bit."""
+    sk = skel()
+    x = syn.uniform_f32(syn.SEED_GRID, 211 * 390, 0.0, 1.0).reshape(211, 390)
+    for kind in ("stencil5", "stencil9"):
+        with forced("chain2d", 0):
+            a = run_chain(sk, kind, boundary, 7, x)
+        with forced("chain2d", 1, 0, 0, k):
+            b = run_chain(sk, kind, boundary, 7, x)
+        assert np.array_equal(a, b), (kind, boundary, k)
+
+
+def test_mapoverlap_chain_periodic_falls_back_and_tmp_rules():
+    sk = skel()
+    x = syn.uniform_f32(syn.SEED_GRID, 40 * 64, 0.0, 1.0).reshape(40, 64)
+    w = oracle.stencil_weights("9pt")
+    with forced("chain2d", 1, 0, 0, 4):
+        with pytest.raises(sk.SkelError):                 # periodic is not time-blocked
+            run_chain(sk, "stencil9", "periodic", 3, x)
+    g = run_chain(sk, "stencil9", "periodic", 3, x)       # dispatched: falls back to per call
+    assert sk.skel_last_variant("chain2d")[0] == 0
+    assert_elem_close(g, oracle.mapoverlap2d_chain_f32(x, 1, w, "periodic", 3), "periodic chain", atol=3e-6)
+    with forced("chain2d", 0):
+        with pytest.raises(sk.SkelError):                 # per call needs tmp for 2+ steps
+            run_chain(sk, "stencil9", "clamp", 2, x, with_tmp=False)
+    with forced("chain2d", 1, 0, 0, 4):                   # one pass covers 3 steps: no tmp needed
+        g = run_chain(sk, "stencil9", "clamp", 3, x, with_tmp=False)
+    assert_elem_close(g, oracle.mapoverlap2d_chain_f32(x, 1, w, "clamp", 3), "single pass", atol=3e-6)

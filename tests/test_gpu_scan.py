@@ -11,9 +11,10 @@ from helpers import assert_prefix_close, dev_empty, dev_tensor, forced, skel, to
 pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
-# (variant, ept, tile); variant 5 with tile 1 publishes the tile aggregate early
+# (variant, ept, tile); variant 5: tile bit 0 publishes the tile aggregate
+# early, bit 1 selects 48 KiB tiles
 SCAN_CONFIGS = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (1, 8, 0), (2, 4, 0), (2, 8, 0), (3, 4, 0), (3, 2, 0),
-                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1)]
+                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1), (5, 4, 2), (5, 4, 3)]
 
 
 def mod32(a):

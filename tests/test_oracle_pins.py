@@ -258,6 +258,30 @@ def test_mapoverlap2d_bwd_is_dense_transpose(boundary, shape, r):
 
 
 @pytest.mark.parametrize("boundary", ["clamp", "zero", "periodic"])
+@pytest.mark.parametrize("shape,steps", [((1, 1), 3), ((6, 5), 1), ((6, 5), 4), ((9, 12), 10)])
+def test_mapoverlap2d_chain_is_matrix_power(boundary, shape, steps):
+    """A chain of k calls is S^k applied to x (numpy matrix power of the
+    dense stencil matrix built with scipy's correlate)."""
+    w = syn.uniform_f32(52, 9, -1.0, 1.0).reshape(3, 3)
+    x = syn.uniform_f32(53, shape[0] * shape[1]).reshape(shape)
+    S = dense_stencil_matrix_2d(shape[0], shape[1], 1, w, boundary)
+    ref = (np.linalg.matrix_power(S, steps) @ x.astype(np.float64).ravel()).reshape(shape)
+    out = oracle.mapoverlap2d_chain_f32(x, 1, w, boundary, steps)
+    assert np.allclose(out, ref, rtol=0, atol=1e-12 * max(1.0, float(np.abs(ref).max())))
+
+
+def test_mapoverlap2d_chain_constant_and_single_step():
+    c = np.full((7, 9), 0.375, np.float32)
+    for kind in ("5pt", "9pt"):
+        assert np.array_equal(oracle.mapoverlap2d_chain_f32(c, 1, oracle.stencil_weights(kind), "clamp", 10),
+                              c.astype(np.float64))
+    x = syn.uniform_f32(54, 63).reshape(7, 9)
+    w = oracle.stencil_weights("9pt")
+    assert np.array_equal(oracle.mapoverlap2d_chain_f32(x, 1, w, "zero", 1), oracle.mapoverlap2d_f32(x, 1, w, "zero"))
+    assert np.array_equal(oracle.mapoverlap2d_chain_f32(x, 1, w, "zero", 0), x.astype(np.float64))
+
+
+@pytest.mark.parametrize("boundary", ["clamp", "zero", "periodic"])
 @pytest.mark.parametrize("r,n", [(1, 1), (1, 9), (3, 5), (16, 40)])
 def test_mapoverlap1d_bwd_is_dense_transpose(boundary, r, n):
     w = syn.uniform_f32(52, 2 * r + 1, -1.0, 1.0)
@@ -300,6 +324,58 @@ def test_rowdot_identity_and_matmul():
     assert np.allclose(out, M.astype(np.float64) @ A.astype(np.float64), rtol=0, atol=1e-12)
     assert np.allclose(ab, np.abs(M.astype(np.float64)) @ np.abs(A.astype(np.float64)),
                        rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------ Coulombic potential ---
+def test_coulomb_pythagorean_distances_and_orientation():
+    """One charge q = 2 at (3, 0, 4) over the plane z0 = 0, spacing 1:
+    distance 5 at the origin, 4 at (x=3, y=0) -- column j = 3 of row i = 0 --
+    and sqrt(34) at (x=0, y=3), which tells the row and column axes apart."""
+    atoms = np.array([[3.0, 0.0, 4.0, 2.0]], np.float32)
+    v, ab = oracle.coulomb_grid_f32(atoms, 4, 4, 1.0, 0.0)
+    assert v[0, 0] == 2.0 / 5.0
+    assert v[0, 3] == 0.5
+    assert v[3, 0] == 2.0 / math.sqrt(34.0)
+    assert np.array_equal(ab, v)                       # one positive charge
+
+
+def test_coulomb_square_of_charges_and_spacing():
+    """Four charges at the corners (3 +- 3, 4 +- 4, 12) of a rectangle; the
+    point below its centre, (3, 4, 0) = grid point (i=8, j=6) at spacing
+    0.5, is 13 from each corner: V = sum q / 13."""
+    q = [1.0, -2.0, 0.5, 4.0]
+    atoms = np.array([[0, 0, 12, q[0]], [6, 0, 12, q[1]], [0, 8, 12, q[2]], [6, 8, 12, q[3]]], np.float32)
+    v, ab = oracle.coulomb_points_f32(atoms, [8], [6], 0.5, 0.0)
+    assert abs(v[0] - sum(q) / 13.0) < 1e-15
+    assert abs(ab[0] - sum(abs(x) for x in q) / 13.0) < 1e-15
+
+
+def test_coulomb_superposition_and_charge_scaling():
+    a = syn.uniform_f32(81, 40 * 4, 0.0, 16.0).reshape(40, 4)
+    a[:, 2] += 1.0                                      # atoms above the plane z0 = 0
+    a[:, 3] = syn.uniform_f32(82, 40)                   # charges in [-1, 1)
+    v_all, _ = oracle.coulomb_grid_f32(a, 9, 7, 2.0, 0.0)
+    v1, _ = oracle.coulomb_grid_f32(a[:17], 9, 7, 2.0, 0.0)
+    v2, _ = oracle.coulomb_grid_f32(a[17:], 9, 7, 2.0, 0.0)
+    assert np.allclose(v_all, v1 + v2, rtol=0, atol=1e-12)
+    b = a.copy()
+    b[:, 3] *= 4.0                                      # exact in float32
+    vb, _ = oracle.coulomb_grid_f32(b, 9, 7, 2.0, 0.0)
+    assert np.allclose(vb, 4.0 * v_all, rtol=1e-15, atol=0)
+
+
+def test_coulomb_far_field_monopole_bound():
+    """Far from a cluster of extent a around c, |V - Q/R| <= sum|q| a / (R (R - a))
+    (triangle inequality on each 1/r)."""
+    a = syn.uniform_f32(83, 25 * 4, -1.0, 1.0).reshape(25, 4)
+    c = np.array([100.0, 200.0, 3.0])
+    a[:, :3] += c.astype(np.float32)
+    ext = float(np.max(np.linalg.norm(a[:, :3].astype(np.float64) - c, axis=1)))
+    Q, Qa = float(a[:, 3].astype(np.float64).sum()), float(np.abs(a[:, 3].astype(np.float64)).sum())
+    for i, j in [(0, 0), (4000, 0), (0, 5000), (3000, 3000)]:
+        v, _ = oracle.coulomb_points_f32(a, [i], [j], 1.0, 0.0)
+        R = float(np.linalg.norm(np.array([j, i, 0.0]) - c))
+        assert abs(v[0] - Q / R) <= Qa * ext / (R * (R - ext)) + 1e-15
 
 
 # -------------------------------------------------------------- Batched ---
