@@ -24,7 +24,9 @@
 //             predecessor per thread;
 //           3 big_tile: 64 KiB frames staged by bulk copies, aggregates
 //             published before the scans, all warps walking the look-back;
-//           4 persistent with warp 0 alone walking the look-back.
+//           4 persistent with warp 0 alone walking the look-back;
+//           5 reduce_then_scan: tile sums, per-instance prefixes, tile scans
+//             (no look-back; the values are read twice).
 #include "scan_tile.cuh"
 
 namespace skel {
@@ -562,25 +564,148 @@ int run_big(const BatchedLaunch &b, Control *ctl, uint64_t *words, unsigned char
     return run_big_k<false, true, true>(b, ctl, words, L, epoch, mt, s);
 }
 
+// ------------------------------------ variant 5: reduce-then-scan ----
+// No look-back at all: (1) every tile's (sum, sum of squares), (2) per
+// instance, the exclusive scan of its tile sums and the total of its sums of
+// squares (one warp per instance, carried in float64), (3) every tile scanned
+// locally and offset by its prefix.  The values are read twice (12 bytes per
+// element with both outputs instead of 8), but no tile ever waits on another.
+template <bool SCAN, bool RED, int V>
+__global__ void __launch_bounds__(kBlock)
+batched_rts_sums(const float *__restrict__ values, const int64_t *__restrict__ off, Layout L, double *aggS,
+                 double *aggQ)
+{
+    constexpr int TILE = kBlock * 4 * V;
+    __shared__ float red[32];
+    const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {          // block-uniform
+        const TileInfo x = tile_info<TILE>(t, total, L, off);
+        float v[V][4];
+        load_masked<V>(values, x.fbase, x.lo, x.hi, v);
+        float ps[V], pq[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            ps[k] = (v[k][0] + v[k][1]) + (v[k][2] + v[k][3]);
+            pq[k] = fmaf(v[k][0], v[k][0], v[k][1] * v[k][1]) + fmaf(v[k][2], v[k][2], v[k][3] * v[k][3]);
+        }
+#pragma unroll
+        for (int st = 1; st < V; st *= 2)
+#pragma unroll
+            for (int i = 0; i + st < V; i += 2 * st) { ps[i] = ps[i] + ps[i + st]; pq[i] = pq[i] + pq[i + st]; }
+        const float as = SCAN ? dev::block_reduce<dev::AddF, float, kBlock>(ps[0], red) : 0.f;
+        const float aq = RED ? dev::block_reduce<dev::AddF, float, kBlock>(pq[0], red) : 0.f;
+        if (threadIdx.x == 0) {
+            aggS[t] = (double)as;
+            aggQ[t] = (double)aq;
+        }
+    }
+}
+
+// One warp per instance: prefS[t] = sum of the instance's tile sums before
+// t; results[b] = sum of its tiles' sums of squares.
+__global__ void __launch_bounds__(kBlock)
+batched_rts_prefix(Layout L, int64_t B, const double *__restrict__ aggS, const double *__restrict__ aggQ,
+                   double *__restrict__ prefS, float *__restrict__ results, int scan, int red)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kBlock / 32);
+    const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+    if (total == 0) return;   // rejected offsets: nothing was laid out
+    for (int64_t b = (int64_t)blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5); b < B; b += warps) {
+        const int64_t s0 = L.tile_start[b], s1 = L.tile_start[b + 1];
+        if (s1 <= s0) continue;                                   // empty: prep wrote its result
+        double carry = 0.0, q = 0.0;
+        for (int64_t k0 = s0; k0 < s1; k0 += 32) {
+            const int64_t k = k0 + lane;
+            const double a = (scan && k < s1) ? aggS[k] : 0.0;
+            if (red && k < s1) q += aggQ[k];
+            const double incl = dev::warp_incl_scan_add(a);
+            if (scan && k < s1) prefS[k] = carry + (incl - a);
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (red) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+            if (lane == 0) results[b] = (float)q;
+        }
+    }
+}
+
+template <bool INCL, int V>
+__global__ void __launch_bounds__(kBlock)
+batched_rts_apply(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ scan_out,
+                  Layout L, const double *__restrict__ prefS)
+{
+    constexpr int TILE = kBlock * 4 * V;
+    __shared__ float smem[kBlock / 32 + 1];
+    const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {          // block-uniform
+        const TileInfo x = tile_info<TILE>(t, total, L, off);
+        float v[V][4];
+        load_masked<V>(values, x.fbase, x.lo, x.hi, v);
+        dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
+        dev::tile_add_prefix<float, V>(v, (float)prefS[t]);
+        store_masked<V>(scan_out, x.fbase, x.lo, x.hi, v);
+    }
+}
+
+template <int V>
+int run_rts(const BatchedLaunch &b, Control *ctl, unsigned char *data, cudaStream_t s)
+{
+    constexpr int TILE = kBlock * 4 * V;
+    const Layout L = layout(data, b, TILE);
+    const int64_t mt = max_tiles(b, TILE);
+    if (mt > 0x7fffffffLL || b.B > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "batched: too many instances or tiles");
+    double *aggS = reinterpret_cast<double *>(data + layout_bytes(b, TILE));
+    double *aggQ = aggS + mt;
+    double *prefS = aggQ + mt;
+    launch_kernel(batched_prep, 1, 1024, 0, s, b.offsets, b.B, b.total, TILE, L, b.results, ctl, mt);
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prep launch");
+    int64_t grid = mt;
+    const int64_t cap = (int64_t)device_info().sms * 64;
+    if (grid > cap) grid = cap;
+    const bool sc = b.want_scan, rd = b.want_reduce;
+    if (sc && rd) launch_kernel(batched_rts_sums<true, true, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, L, aggS, aggQ);
+    else if (sc) launch_kernel(batched_rts_sums<true, false, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, L, aggS, aggQ);
+    else launch_kernel(batched_rts_sums<false, true, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, L, aggS, aggQ);
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched sums launch");
+    const int64_t pgrid = ceil_div(b.B, kBlock / 32) < 4096 ? ceil_div(b.B, kBlock / 32) : 4096;
+    launch_kernel(batched_rts_prefix, (unsigned)pgrid, kBlock, 0, s, L, b.B, aggS, aggQ, prefS, b.results, (int)sc,
+                  (int)rd);
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prefix launch");
+    if (!sc) return SKEL_OK;
+    if (b.inclusive) launch_kernel(batched_rts_apply<true, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.scan_out, L, prefS);
+    else launch_kernel(batched_rts_apply<false, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.scan_out, L, prefS);
+    e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "batched apply launch");
+}
+
 }  // namespace
 
-int batched_variant_count() { return 5; }
+int batched_variant_count() { return 6; }
 const char *batched_variant_name(int v)
 {
     static const char *names[] = {"persistent", "one_per_tile", "persistent_block_lookback", "big_tile",
-                                  "persistent_warp_lookback"};
-    return v >= 0 && v < 5 ? names[v] : "?";
+                                  "persistent_warp_lookback", "reduce_then_scan"};
+    return v >= 0 && v < 6 ? names[v] : "?";
 }
 Choice batched_default() { return Choice{3, 256, 4, 0}; }
 
-size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c) { return layout_bytes(b, tile_of(c)); }
+size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c)
+{
+    // reduce-then-scan also keeps three float64 values per tile
+    return layout_bytes(b, tile_of(c)) + (c.variant == 5 ? 3 * 8 * (size_t)max_tiles(b, tile_of(c)) : 0);
+}
 // aggregate and prefix of every tile, two words (scan carry, sum of squares) each
 size_t batched_word_count(const BatchedLaunch &b, const Choice &c) { return 4 * (size_t)max_tiles(b, tile_of(c)); }
 
 int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, unsigned char *data,
                    uint32_t epoch, cudaStream_t s)
 {
-    if (c.variant < 0 || c.variant > 4) return fail(SKEL_ERR_INVALID_ARG, "batched: unknown variant");
+    if (c.variant < 0 || c.variant > 5) return fail(SKEL_ERR_INVALID_ARG, "batched: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "batched: block must be 256");
     if (!aligned16(b.values) || (b.scan_out && !aligned16(b.scan_out)))
         return fail(SKEL_ERR_UNSUPPORTED, "batched: values and scan_out must be 16-byte aligned");
@@ -588,6 +713,13 @@ int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64
     if (c.variant == 3) {
         if (c.ept > 0 && c.ept != kBigV) return fail(SKEL_ERR_INVALID_ARG, "batched big: ept must be 4");
         return run_big(b, ctl, words, data, epoch, s);
+    }
+    if (c.variant == 5) {
+        switch (c.ept > 0 ? c.ept : 4) {
+        case 4: return run_rts<4>(b, ctl, data, s);
+        case 8: return run_rts<8>(b, ctl, data, s);
+        default: return fail(SKEL_ERR_INVALID_ARG, "batched reduce-then-scan: ept must be 4 or 8");
+        }
     }
     switch (c.ept > 0 ? c.ept : 4) {
     case 2: return run_v<2>(b, c, ctl, words, data, epoch, s);

@@ -108,6 +108,8 @@ def candidates(sk_name: str):
             for e in (2, 4, 8):
                 yield (v, 256, e, 0)
         yield (3, 256, 4, 0)
+        yield (5, 256, 4, 0)
+        yield (5, 256, 8, 0)
 
 
 class Instance:

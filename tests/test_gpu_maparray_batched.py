@@ -60,7 +60,8 @@ def check_batched(v, off, res, scan, inclusive):
         assert_prefix_close(scan, ref, ab, "batched scan")
 
 
-@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8), (2, 4), (1, 8), (3, 4), (4, 4), (4, 8)])
+@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8), (2, 4), (1, 8), (3, 4), (4, 4), (4, 8), (5, 4),
+                                         (5, 8)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_batched_small_mixed(variant, ept, inclusive):
     """Empty, tiny, unaligned and multi-tile instances mixed."""
@@ -77,7 +78,7 @@ def test_batched_small_mixed(variant, ept, inclusive):
     check_batched(v, off, to_np(res), to_np(sc), inclusive)
 
 
-@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("variant", [0, 3, 5])
 def test_batched_only_reduce_and_only_scan(variant):
     import torch
     sk = skel()
@@ -98,7 +99,7 @@ def _only_reduce_only_scan(sk, torch):
     check_batched(v, off, to_np(res), to_np(sc), True)
 
 
-@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("variant", [0, 3, 5])
 def test_batched_full_workload_and_graph_plan(variant):
     """4096 instances, log-uniform lengths in [64, 2^20] (~4.4e8 elements):
     direct call, captured plan replayed twice, and per-instance calls on a
@@ -144,13 +145,19 @@ def _full_workload(sk, torch):
         view.close()
 
 
-def test_batched_rejects_bad_offsets():
+@pytest.mark.parametrize("variant", [-1, 5])
+def test_batched_rejects_bad_offsets(variant):
     import torch
     sk = skel()
     v = torch.zeros(100, device="cuda")
     off = torch.tensor([0, 50, 40, 100], dtype=torch.int64, device="cuda")   # decreasing
     res = torch.zeros(3, device="cuda")
-    sk.skel_batched(wrap(v), wrap(off), wrap(res), None, True)
+    sc = torch.zeros(100, device="cuda")
+    sk.skel_force_variant("batched", variant)
+    try:
+        sk.skel_batched(wrap(v), wrap(off), wrap(res), wrap(sc), True)
+    finally:
+        sk.skel_force_variant("batched", -1)
     with pytest.raises(sk.SkelError):
         sk.skel_check_device()
     sk.skel_check_device()   # the status was cleared by the previous check
