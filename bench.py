@@ -479,6 +479,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-default", action="store_true", help="profiling: skip the default-variant leg")
+    ap.add_argument("--no-next", action="store_true", help="profiling: skip the Coulombic-potential leg")
     ap.add_argument("--only", default=None,
                     help="profiling: comma-separated call names; times only those calls (no default-variant, "
                          "e2e or CPU legs)")
@@ -589,7 +590,7 @@ def main():
             "input_gen_s": round(wl.gen_s, 1)}
     del wl, calls
     torch.cuda.empty_cache()
-    if not args.only and not args.force:
+    if not args.only and not args.force and not args.no_next:
         line["next"] = {"coulomb_grid": coulomb_leg(sk, torch, stream, clocks)}
     if not args.no_e2e:
         dt, h2d, d2h, cpus, per_step = e2e_run(sk, torch, min(args.steps, 5), stream)

@@ -692,7 +692,7 @@ const char *batched_variant_name(int v)
                                   "persistent_warp_lookback", "reduce_then_scan"};
     return v >= 0 && v < 6 ? names[v] : "?";
 }
-Choice batched_default() { return Choice{3, 256, 4, 0}; }
+Choice batched_default() { return Choice{5, 256, 4, 0}; }
 
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c)
 {
