@@ -639,7 +639,10 @@ batched_rts_apply(const float *__restrict__ values, const int64_t *__restrict__ 
     constexpr int TILE = kBlock * 4 * V;
     __shared__ float smem[kBlock / 32 + 1];
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {          // block-uniform
+    // last tiles first: the sums pass read the values in increasing order, so
+    // its most recent tiles are still in L2 when this pass starts
+    for (int64_t k = blockIdx.x; k < total; k += gridDim.x) {          // block-uniform
+        const int64_t t = total - 1 - k;
         const TileInfo x = tile_info<TILE>(t, total, L, off);
         float v[V][4];
         load_masked<V>(values, x.fbase, x.lo, x.hi, v);

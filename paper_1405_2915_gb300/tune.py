@@ -325,6 +325,38 @@ def bucket(n: int) -> int:
     return min(15, (int(n).bit_length() - 1) // 2)
 
 
+def adaptive_sizes(sizes, decide, key, stride: int = 3):
+    """Adaptive sampling over the size buckets: decide() every stride-th size
+    and the last one; between two sampled sizes whose decisions (compared by
+    key) differ, decide the middle one and recurse on both halves.  A run of
+    buckets bounded by two equal decisions is left unsampled (None) and takes
+    that decision (a change and its undoing within one stride go unseen; the
+    validation between buckets still checks every bucket against the
+    default).  Returns {size: decide(size) or None}."""
+    got = {}
+
+    def d(i):
+        if i not in got:
+            got[i] = decide(sizes[i])
+        return got[i]
+
+    def rec(lo, hi):
+        if hi - lo <= 1 or key(d(lo)) == key(d(hi)):
+            return
+        mid = (lo + hi) // 2
+        d(mid)
+        rec(lo, mid)
+        rec(mid, hi)
+
+    if sizes:
+        coarse = sorted(set(list(range(0, len(sizes), stride)) + [len(sizes) - 1]))
+        for i in coarse:
+            d(i)
+        for lo, hi in zip(coarse, coarse[1:]):
+            rec(lo, hi)
+    return {n: got.get(i) for i, n in enumerate(sizes)}
+
+
 def tune(args):
     timer = Timer()
     lines = ["# execution-plan table of libskel.so, written by paper_1405_2915_gb300.tune on "
@@ -332,12 +364,16 @@ def tune(args):
              "# skeleton fn dtype bucket radius residency variant block ept tile"]
     report = ["| skeleton instance | n | default GB/s | tuned GB/s | speedup | chosen |", "|---|---|---|---|---|---|"]
     chosen_all = []
+    samples_taken = samples_full = 0
     skel_load_dispatch_table(None)
     for inst in instances(args.nmax_log2):
         if args.only and not any(s in inst.name for s in args.only):
             continue
         sk_id = SK[inst.sk_name]
-        for n in inst.sizes:
+
+        def decide(n):
+            """Times the default and every candidate at n (and 2n); returns
+            (choice or None, default ms, chosen ms, bytes)."""
             # a bucket spans [n, 4n): a candidate must beat the default both
             # at its lower edge and in its middle (2n) to be chosen
             pts = [n] + ([2 * n] if 2 * n <= inst.nmax else [])
@@ -375,20 +411,36 @@ def tune(args):
                 t_best2 = time_cand(best)
                 if not max(t / td for t, td in zip(t_best2, t_def2)) < 1.0 - args.margin:
                     best = None
+            return best, t_def[0], (t_best[0] if best is not None else t_def[0]), nbs[0]
+
+        if args.adaptive:
+            measured = adaptive_sizes(inst.sizes, lambda n: decide(n), key=lambda r: r[0])
+        else:
+            measured = {n: decide(n) for n in inst.sizes}
+        samples_taken += sum(1 for v in measured.values() if v is not None)
+        samples_full += len(inst.sizes)
+        last = None
+        for n in inst.sizes:
+            r = measured.get(n)
+            sampled = r is not None
+            r = r if sampled else last          # unsampled: its sampled neighbours agree
+            last = r
+            best, t_def, t_tuned, nb = r
             if best is not None:
                 lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 "
                              f"{best[0]} {best[1]} {best[2]} {best[3]}")
                 chosen = best
-                t_tuned = t_best[0]
             else:
                 # record that the default won here, so this bucket never
                 # inherits a neighbouring bucket's choice by extrapolation
                 lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 -1 0 0 0")
-                chosen, t_tuned = "default", t_def[0]
-            nb, t_def = nbs[0], t_def[0]
+                chosen = "default"
             chosen_all.append((inst.name, n, chosen))
-            report.append(f"| {inst.name} | {n} | {nb / t_def / 1e6:.1f} | {nb / t_tuned / 1e6:.1f} | "
-                          f"{t_def / t_tuned:.3f} | {chosen} |")
+            if sampled:
+                report.append(f"| {inst.name} | {n} | {nb / t_def / 1e6:.1f} | {nb / t_tuned / 1e6:.1f} | "
+                              f"{t_def / t_tuned:.3f} | {chosen} |")
+            else:
+                report.append(f"| {inst.name} | {n} | - | - | - | {chosen} (not sampled: neighbours agree) |")
             print(report[-1], flush=True)
     if not args.only or "batched" in args.only:
         total, fn, nb = batched_instance()
@@ -414,6 +466,8 @@ def tune(args):
         print(report[-1], flush=True)
     with open(args.out, "w") as f:
         f.write("\n".join(lines) + "\n")
+    report.append(f"\nsize buckets sampled: {samples_taken} of {samples_full}"
+                  + (" (adaptive)" if args.adaptive else ""))
     return report
 
 
@@ -452,6 +506,8 @@ def main():
     ap.add_argument("--only", nargs="*", default=None)
     ap.add_argument("--no-validate", action="store_true")
     ap.add_argument("--verbose", action="store_true", help="log every candidate's time")
+    ap.add_argument("--adaptive", action="store_true",
+                    help="sample size buckets adaptively (refine only where the choice changes)")
     args = ap.parse_args()
     t0 = time.time()
     report = tune(args)

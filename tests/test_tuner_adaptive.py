@@ -1,0 +1,47 @@
+"""Adaptive sampling of the tuner's size buckets (host logic, no GPU): only
+the buckets needed to locate where the best variant changes are timed."""
+import pytest
+
+tune = pytest.importorskip("paper_1405_2915_gb300.tune")
+
+
+def run(truth):
+    sizes = list(range(len(truth)))
+    calls = []
+
+    def decide(n):
+        calls.append(n)
+        return truth[n]
+
+    got = tune.adaptive_sizes(sizes, decide, key=lambda r: r)
+    filled, last = [], None
+    for n in sizes:
+        last = got[n] if got[n] is not None else last
+        filled.append(last)
+    return filled, calls
+
+
+def test_constant_choice_samples_only_the_coarse_grid():
+    filled, calls = run(["a"] * 10)
+    assert filled == ["a"] * 10
+    assert sorted(calls) == [0, 3, 6, 9]
+
+
+@pytest.mark.parametrize("k", range(1, 10))
+def test_one_change_point_is_located_exactly(k):
+    truth = ["small"] * k + ["large"] * (10 - k)
+    filled, calls = run(truth)
+    assert filled == truth
+    assert len(calls) <= 4 + 2          # the coarse grid plus a bisection of one stride
+    assert len(set(calls)) == len(calls)  # no bucket timed twice
+
+
+def test_several_changes_are_all_found():
+    truth = ["d", "d", "v1", "v1", "v1", "v2", "v2", "d", "d", "d"]
+    filled, calls = run(truth)
+    assert filled == truth
+
+
+def test_empty_and_single():
+    assert tune.adaptive_sizes([], lambda n: 1, key=lambda r: r) == {}
+    assert tune.adaptive_sizes([5], lambda n: "x", key=lambda r: r) == {5: "x"}
