@@ -348,8 +348,10 @@ def bind_to_gpu_local_cpus(torch, device_index: int):
 
 def e2e_run(sk, torch, steps, stream):
     """The same step through the public API with host buffers: inputs live in
-    pinned host memory and are copied lazily by the containers (H2D inside
-    the timed region), results are read back to the host (D2H)."""
+    pinned host memory and reach the device through the containers (H2D
+    inside the timed region: prefetched on a copy stream in order of first
+    use, so that copies overlap the calls), and every result is copied back
+    to the host (D2H on a second copy stream as soon as it is final)."""
     cpus = bind_to_gpu_local_cpus(torch, torch.cuda.current_device())
     dev = torch.device("cuda")
     pin = lambda a: torch.from_numpy(a).pin_memory()
@@ -374,31 +376,39 @@ def e2e_run(sk, torch, steps, stream):
     co = {k: C.empty(s) for k, s in outs.items()}
     co["oI"] = C.empty((N,), np.int32)
     c = {**ci, **co}
+    # (call, results final after it): each result starts its copy back to the
+    # host as soon as no later call of the step writes it
     calls = [
-        lambda: sk.skel_map("axpy", [c["x"], c["y"]], c["oA"], [2.5]),
-        lambda: sk.skel_reduce("add", c["x"], c["r1"], host=False),
-        lambda: sk.skel_reduce("max", c["x"], c["r1"], host=False),
-        lambda: sk.skel_mapreduce("mul", "add", [c["x"], c["y"]], c["r1"], host=False),
-        lambda: sk.skel_scan("add", True, c["xi"], c["oI"]),
-        lambda: sk.skel_scan("add", False, c["x"], c["oB"]),
-        lambda: sk.skel_mapoverlap("stencil9", 1, None, "clamp", c["grid"], c["oG"]),
-        lambda: sk.skel_mapoverlap("stencil5", 1, None, "clamp", c["grid"], c["oG2"]),
-        lambda: sk.skel_mapoverlap("stencil1d", R1D, None, "clamp", c["x"], c["oA"]),
-        lambda: sk.skel_maparray("rowdot", c["A"], c["M"], c["rd"]),
-        lambda: sk.skel_maparray("gather", c["Ag"], c["idx"], c["oB"]),
-        lambda: sk.skel_batched(c["bv"], c["boff"], c["bres"], c["bsc"], True),
-        lambda: sk.skel_map_bwd("tanh", [c["y"]], c["x"], [c["oA"]], [1.0]),
-        lambda: sk.skel_scan_bwd("add", True, c["x"], c["oB"]),
-        lambda: sk.skel_mapoverlap_bwd("stencil9", 1, None, "clamp", c["grid"], c["oG"]),
+        (lambda: sk.skel_map("axpy", [c["x"], c["y"]], c["oA"], [2.5]), []),
+        (lambda: sk.skel_reduce("add", c["x"], c["r1"], host=False), []),
+        (lambda: sk.skel_reduce("max", c["x"], c["r1"], host=False), []),
+        (lambda: sk.skel_mapreduce("mul", "add", [c["x"], c["y"]], c["r1"], host=False), ["r1"]),
+        (lambda: sk.skel_scan("add", True, c["xi"], c["oI"]), ["oI"]),
+        (lambda: sk.skel_scan("add", False, c["x"], c["oB"]), []),
+        (lambda: sk.skel_mapoverlap("stencil9", 1, None, "clamp", c["grid"], c["oG"]), []),
+        (lambda: sk.skel_mapoverlap("stencil5", 1, None, "clamp", c["grid"], c["oG2"]), ["oG2"]),
+        (lambda: sk.skel_mapoverlap("stencil1d", R1D, None, "clamp", c["x"], c["oA"]), []),
+        (lambda: sk.skel_maparray("rowdot", c["A"], c["M"], c["rd"]), ["rd"]),
+        (lambda: sk.skel_maparray("gather", c["Ag"], c["idx"], c["oB"]), []),
+        (lambda: sk.skel_batched(c["bv"], c["boff"], c["bres"], c["bsc"], True), ["bres", "bsc"]),
+        (lambda: sk.skel_map_bwd("tanh", [c["y"]], c["x"], [c["oA"]], [1.0]), ["oA"]),
+        (lambda: sk.skel_scan_bwd("add", True, c["x"], c["oB"]), ["oB"]),
+        (lambda: sk.skel_mapoverlap_bwd("stencil9", 1, None, "clamp", c["grid"], c["oG"]), ["oG"]),
     ]
     read_back = ["oA", "oB", "oI", "oG", "oG2", "rd", "bres", "bsc", "r1"]
+    first_use = ["x", "y", "xi", "grid", "A", "M", "Ag", "idx", "bv", "boff"]
+    h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
 
     def one_step():
         for k in ci:                       # the host copies hold this step's inputs
             ci[k].mark(sk.UNIT_HOST)
-        for fn in calls:
+        for k in first_use:                # inputs start moving in order of first use
+            ci[k].prefetch(sk.UNIT_DEVICE, h2d)
+        for fn, done in calls:
             fn()
-        for k in read_back:                # results to the host
+            for k in done:                 # final results start moving back at once
+                c[k].prefetch(sk.UNIT_HOST, d2h)
+        for k in read_back:                # host reads wait for their copies
             c[k].host_ptr(sk.READ, stream)
 
     def stats():

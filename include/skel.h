@@ -188,6 +188,15 @@ int skel_container_device_ptr(skel_handle h, int mode, void *stream, void **ptr)
  * wrapped pointer): the valid set becomes exactly `units`. */
 int skel_container_mark(skel_handle h, int units);
 
+/* Starts, without waiting, the copy that makes `unit` (SKEL_UNIT_HOST or
+ * SKEL_UNIT_DEVICE) hold a valid copy: the lazy copy of Sec. IV issued
+ * early, so that it overlaps other work.  Enqueued on `stream` after the
+ * container's last device use (on whatever stream that was); later accesses
+ * order after it (a host access waits for it).  Nothing is copied when
+ * `unit` is already valid or no unit is.  A host copy is allocated (pinned)
+ * if the container has none. */
+int skel_container_prefetch(skel_handle h, int unit, void *stream);
+
 /* Shape and state: dtype, ndim, shape[2] (shape[1] = 1 for 1D), bits of the
  * units that currently hold a valid copy. */
 int skel_container_info(skel_handle h, int *dtype, int *ndim, int64_t *shape, int *valid_units);

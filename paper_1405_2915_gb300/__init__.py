@@ -170,6 +170,10 @@ class Container:
     def mark(self, units: int) -> None:
         check(lib.skel_container_mark(self.handle, units))
 
+    def prefetch(self, unit: int, stream=None) -> None:
+        """Starts the copy that makes `unit` valid, on `stream`, without waiting."""
+        check(lib.skel_container_prefetch(self.handle, unit, _stream(stream)))
+
     def to_numpy(self, stream=None) -> np.ndarray:
         """Host read access (lazy device->host copy), returned as a copy."""
         dt, shape, _ = self.info()

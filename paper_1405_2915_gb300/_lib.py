@@ -41,6 +41,7 @@ SIGNATURES = {
     "skel_container_host_ptr": (i32, [vp, i32, vp, C.POINTER(vp)]),
     "skel_container_device_ptr": (i32, [vp, i32, vp, C.POINTER(vp)]),
     "skel_container_mark": (i32, [vp, i32]),
+    "skel_container_prefetch": (i32, [vp, i32, vp]),
     "skel_container_info": (i32, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i64), C.POINTER(i32)]),
     "skel_container_stats": (i32, [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
     "skel_container_destroy": (i32, [vp]),

@@ -306,6 +306,34 @@ int skel_container_mark(skel_handle h, int units)
     });
 }
 
+int skel_container_prefetch(skel_handle h, int unit, void *stream)
+{
+    return guarded([&] {
+        if (!valid_handle(h)) return fail(SKEL_ERR_INVALID_ARG, "bad handle");
+        if (unit != SKEL_UNIT_HOST && unit != SKEL_UNIT_DEVICE) return fail(SKEL_ERR_INVALID_ARG, "unknown unit");
+        Storage *st = h->st;
+        if ((st->valid & unit) || st->valid == 0) return (int)SKEL_OK;
+        cudaStream_t s = (cudaStream_t)stream;
+        if (unit == SKEL_UNIT_DEVICE) {
+            void *p = nullptr;
+            return acquire_device(h, SKEL_READ, s, &p);   // enqueues the copy, does not wait
+        }
+        if (!st->host) {
+            SKEL_CUDA_TRY(cudaMallocHost(&st->host, st->bytes ? st->bytes : 1));
+            st->host_owned = true;
+        }
+        int rc = order_after_last_use(st, s);
+        if (rc) return rc;
+        SKEL_CUDA_TRY(cudaMemcpyAsync(st->host, st->dev, st->bytes, cudaMemcpyDeviceToHost, s));
+        st->d2h_count += 1;
+        st->d2h_bytes += (int64_t)st->bytes;
+        st->valid |= SKEL_UNIT_HOST;          // a read copy: both units valid
+        st->last_stream = s;                  // a host access waits for this stream
+        st->used_on_device = true;
+        return (int)SKEL_OK;
+    });
+}
+
 int skel_container_info(skel_handle h, int *dtype, int *ndim, int64_t *shape, int *valid_units)
 {
     return guarded([&] {

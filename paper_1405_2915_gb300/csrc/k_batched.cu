@@ -632,7 +632,7 @@ batched_rts_prefix(Layout L, int64_t B, const double *__restrict__ aggS, const d
 }
 
 template <bool INCL, int V>
-__global__ void __launch_bounds__(kBlock, V <= 4 ? 6 : 3)
+__global__ void __launch_bounds__(kBlock, V <= 4 ? 1 : 3)
 batched_rts_apply(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ scan_out,
                   Layout L, const double *__restrict__ prefS)
 {

@@ -149,3 +149,40 @@ def test_residency_enters_dispatch_key():
         assert sk.skel_last_variant("map")[0] == 2
     finally:
         sk.skel_load_dispatch_table(None)
+
+
+def test_prefetch_both_directions_overlaps_and_counts():
+    """Prefetch copies on their own streams; the skeleton on the current
+    stream and the host read order after them; each copy happens once."""
+    import torch
+    sk = skel()
+    n = 1 << 22
+    x = syn.uniform_f32(syn.SEED_X, n)
+    y = syn.uniform_f32(syn.SEED_Y, n)
+    cx, cy = sk.Container.from_host(x.copy()), sk.Container.from_host(y.copy())
+    out = sk.Container.empty((n,))
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    cx.prefetch(sk.UNIT_DEVICE, s_in)
+    cy.prefetch(sk.UNIT_DEVICE, s_in)
+    cy.prefetch(sk.UNIT_DEVICE, s_in)                  # already on its way: no second copy
+    sk.skel_map("axpy", [cx, cy], out, [2.5])
+    out.prefetch(sk.UNIT_HOST, s_out)
+    got = out.to_numpy()
+    assert_elem_close(got, oracle.map_f32("axpy", x, y, 2.5), "axpy after prefetch")
+    assert cx.stats()["h2d"] == 1 and cy.stats()["h2d"] == 1
+    assert out.stats()["d2h"] == 1                      # the host read found the prefetched copy
+    out.prefetch(sk.UNIT_HOST, s_out)                   # valid already: nothing to do
+    assert out.stats()["d2h"] == 1
+    # a later device write after the prefetch waits for it (write-after-read)
+    sk.skel_map("scale", [cx], out, [0.5])
+    assert_elem_close(out.to_numpy(), oracle.map_f32("scale", x, None, 0.5), "write after prefetch")
+    for c in (cx, cy, out):
+        c.close()
+
+
+def test_prefetch_rejects_bad_unit():
+    sk = skel()
+    c = sk.Container.from_host(np.zeros(16, np.float32))
+    with pytest.raises(sk.SkelError):
+        c.prefetch(3)
+    c.close()
