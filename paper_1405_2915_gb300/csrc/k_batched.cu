@@ -638,16 +638,21 @@ batched_rts_apply(const float *__restrict__ values, const int64_t *__restrict__ 
 {
     constexpr int TILE = kBlock * 4 * V;
     __shared__ float smem[kBlock / 32 + 1];
+    __shared__ float s_pre[2];
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
     // last tiles first: the sums pass read the values in increasing order, so
     // its most recent tiles are still in L2 when this pass starts
-    for (int64_t k = blockIdx.x; k < total; k += gridDim.x) {          // block-uniform
+    int par = 0;
+    for (int64_t k = blockIdx.x; k < total; k += gridDim.x, par ^= 1) {   // block-uniform
         const int64_t t = total - 1 - k;
         const TileInfo x = tile_info<TILE>(t, total, L, off);
         float v[V][4];
         load_masked<V>(values, x.fbase, x.lo, x.hi, v);
+        // one float64 -> float32 conversion per tile, read after the scan's
+        // barriers; two slots, so the next tile's write cannot overtake a read
+        if (threadIdx.x == 0) s_pre[par] = (float)prefS[t];
         dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
-        dev::tile_add_prefix<float, V>(v, (float)prefS[t]);
+        dev::tile_add_prefix<float, V>(v, s_pre[par]);
         store_masked<V>(scan_out, x.fbase, x.lo, x.hi, v);
     }
 }

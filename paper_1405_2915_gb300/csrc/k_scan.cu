@@ -444,12 +444,15 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
             else dev::Codec<CT>::put(d.agg + tile * W, (CT)tile_agg, epoch);
         }
     }
-    // pass A: scan every sub-tile in place; carries between sub-tiles in CT
-    CT carry[SUB];
-    CT run = CT(0);
+    // pass A: scan every sub-tile in place.  The carries between sub-tiles
+    // are block-uniform and kept by thread 0 alone, in CT (a float64 add in
+    // every thread would load the slow float64 pipe for nothing).
+    __shared__ CT s_carry[SUB];
+    __shared__ T s_pre[SUB];
+    CT run = CT(0);                                          // meaningful in thread 0
 #pragma unroll
     for (int j = 0; j < SUB; ++j) {
-        carry[j] = run;
+        if (threadIdx.x == 0) s_carry[j] = run;
         const int64_t off = (int64_t)j * kTmaTile;
         if (kProgressive && !EARLY && !wait_chunks(j, j + 1)) return;   // block-uniform
         if (off >= len) continue;                                       // block-uniform
@@ -459,7 +462,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         const T agg = dev::tile_scan_local<T, INCL, kBlock, kTmaV>(v, smem);
 #pragma unroll
         for (int k = 0; k < kTmaV; ++k) put4(off + w * 128 * kTmaV + k * 128 + lane * 4, v[k]);   // own slots
-        run = run + (CT)agg;
+        if (threadIdx.x == 0) run = run + (CT)agg;
     }
     // EARLY: the aggregate is out already and the walk publishes the
     // inclusive prefix from that same value, so successors see one
@@ -468,6 +471,11 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
                                                              false, pub && tile != first, lbs)
                        : dev::wide_lookback<CT, kBlock / 32>(tile, first, run, d, epoch, ctl, limit_ns, pub, pub, lbs);
     // pass B: add the prefix and store, sub-tile by sub-tile
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < SUB; ++j) s_pre[j] = dev::to_elem<T>(p + s_carry[j]);
+    }
+    __syncthreads();
 #pragma unroll
     for (int j = 0; j < SUB; ++j) {
         const int64_t off = (int64_t)j * kTmaTile;
@@ -475,7 +483,7 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         T v[kTmaV][4];
 #pragma unroll
         for (int k = 0; k < kTmaV; ++k) get4(off + w * 128 * kTmaV + k * 128 + lane * 4, v[k]);
-        dev::tile_add_prefix<T, kTmaV>(v, dev::to_elem<T>(p + carry[j]));
+        dev::tile_add_prefix<T, kTmaV>(v, s_pre[j]);
         TileMap ms;
         ms.rev = rev;
         ms.base = rev ? m.base - off : m.base + off;

@@ -285,6 +285,8 @@ struct WideLookbackSmem {
     CT sum[NW];
     int incl[NW];     // 1 if the warp's window holds a published prefix
     CT result;
+    CT total;         // the running exclusive prefix after a round
+    int found;        // the round reached a published prefix
 };
 
 // pub_agg: publish the aggregate first (false when the caller already has);
@@ -340,17 +342,25 @@ __device__ __forceinline__ CT wide_lookback(int64_t tile, int64_t first, CT agg,
             sm.incl[w] = incl_mask != 0u;
         }
         __syncthreads();
-        // nearest window with a published prefix; sum the windows up to it
-        CT s = CT(0);
-        bool found = false;
+        // nearest window with a published prefix; sum the windows up to it.
+        // One thread adds (float64 is a slow pipe on this part) and the
+        // others read the result.
+        if (threadIdx.x == 0) {
+            CT s = CT(0);
+            bool found = false;
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            if (!found) {
-                s = s + sm.sum[k];
-                found = sm.incl[k] != 0;
+            for (int k = 0; k < NW; ++k) {
+                if (!found) {
+                    s = s + sm.sum[k];
+                    found = sm.incl[k] != 0;
+                }
             }
+            sm.total = excl + s;
+            sm.found = found;
         }
-        excl = excl + s;
+        __syncthreads();
+        excl = sm.total;
+        const bool found = sm.found;
         __syncthreads();   // sm is rewritten by the next round
         if (found) break;
         pred -= 32 * NW;
