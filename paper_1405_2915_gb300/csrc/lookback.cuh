@@ -282,11 +282,10 @@ __device__ __forceinline__ CT block_lookback(int64_t tile, int64_t first, CT agg
 // ready.  Returns the exclusive prefix in every thread.
 template <class CT, int NW>
 struct WideLookbackSmem {
-    CT sum[NW];
-    int incl[NW];     // 1 if the warp's window holds a published prefix
-    CT result;
-    CT total;         // the running exclusive prefix after a round
-    int found;        // the round reached a published prefix
+    CT vals[32 * NW];   // each lane's predecessor value of the round (0 past a published prefix)
+    int incl[NW];       // 1 if the warp's window holds a published prefix
+    CT total;           // the running exclusive prefix after a round
+    int found;          // the round reached a published prefix
 };
 
 // pub_agg: publish the aggregate first (false when the caller already has);
@@ -335,28 +334,27 @@ __device__ __forceinline__ CT wide_lookback(int64_t tile, int64_t first, CT agg,
         }
         const unsigned lim = incl_mask ? (((incl_mask & (0u - incl_mask)) << 1) - 1u) : 0xffffffffu;
         if (!((lim >> lane) & 1u) || status == 0) val = CT(0);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) val = val + shfl_xor_ct(val, o);
-        if (lane == 0) {
-            sm.sum[w] = val;
-            sm.incl[w] = incl_mask != 0u;
-        }
+        sm.vals[w * 32 + lane] = val;
+        if (lane == 0) sm.incl[w] = incl_mask != 0u;
         __syncthreads();
-        // nearest window with a published prefix; sum the windows up to it.
-        // One thread adds (float64 is a slow pipe on this part) and the
-        // others read the result.
-        if (threadIdx.x == 0) {
-            CT s = CT(0);
-            bool found = false;
+        // Warp 0 adds the windows up to the nearest one holding a published
+        // prefix: lane l sums entry l of each of those windows, then one tree
+        // over the lanes.  (float64 is a slow pipe on this part: this takes
+        // k + 5 warp-wide adds for k windows, not 5 in every warp.)
+        if (w == 0) {
+            int kmax = NW - 1;
+            bool found_any = false;
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                if (!found) {
-                    s = s + sm.sum[k];
-                    found = sm.incl[k] != 0;
-                }
+            for (int k = NW - 1; k >= 0; --k)
+                if (sm.incl[k]) { kmax = k; found_any = true; }
+            CT acc = CT(0);
+            for (int k = 0; k <= kmax; ++k) acc = acc + sm.vals[k * 32 + lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = acc + shfl_xor_ct(acc, o);
+            if (lane == 0) {
+                sm.total = excl + acc;
+                sm.found = found_any;
             }
-            sm.total = excl + s;
-            sm.found = found;
         }
         __syncthreads();
         excl = sm.total;
