@@ -570,16 +570,42 @@ int run_big(const BatchedLaunch &b, Control *ctl, uint64_t *words, unsigned char
 // squares (one warp per instance, carried in float64), (3) every tile scanned
 // locally and offset by its prefix.  The values are read twice (12 bytes per
 // element with both outputs instead of 8), but no tile ever waits on another.
+// Per-tile placement for the reduce-then-scan passes, computed once in
+// parallel: one 32-byte load per tile there instead of three dependent ones
+// (tile -> instance -> offsets), and its address is known a tile ahead.
+struct __align__(16) TileMeta {
+    int64_t fbase, lo, hi, pad;
+};
+
+template <int TILE>
+__global__ void __launch_bounds__(kBlock)
+batched_meta(const int64_t *__restrict__ off, Layout L, TileMeta *__restrict__ meta)
+{
+    const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+    for (int64_t t = (int64_t)blockIdx.x * kBlock + threadIdx.x; t < total; t += (int64_t)gridDim.x * kBlock) {
+        const TileInfo x = tile_info<TILE>(t, total, L, off);
+        meta[t] = TileMeta{x.fbase, x.lo, x.hi, 0};
+    }
+}
+
+__device__ __forceinline__ TileMeta load_meta(const TileMeta *meta, int64_t t)
+{
+    const longlong2 *p = reinterpret_cast<const longlong2 *>(meta + t);
+    const longlong2 a = __ldg(p), b = __ldg(p + 1);
+    return TileMeta{a.x, a.y, b.x, b.y};
+}
+
 template <bool SCAN, bool RED, int V>
 __global__ void __launch_bounds__(kBlock)
-batched_rts_sums(const float *__restrict__ values, const int64_t *__restrict__ off, Layout L, double *aggS,
+batched_rts_sums(const float *__restrict__ values, const TileMeta *__restrict__ meta, Layout L, double *aggS,
                  double *aggQ)
 {
-    constexpr int TILE = kBlock * 4 * V;
     __shared__ float red[32];
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
+    TileMeta x = blockIdx.x < total ? load_meta(meta, blockIdx.x) : TileMeta{0, 0, 0, 0};
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {          // block-uniform
-        const TileInfo x = tile_info<TILE>(t, total, L, off);
+        const int64_t tn = t + gridDim.x;
+        const TileMeta xn = tn < total ? load_meta(meta, tn) : x;       // the next tile's placement, in flight
         float v[V][4];
         load_masked<V>(values, x.fbase, x.lo, x.hi, v);
         float ps[V], pq[V];
@@ -598,6 +624,7 @@ batched_rts_sums(const float *__restrict__ values, const int64_t *__restrict__ o
             aggS[t] = (double)as;
             aggQ[t] = (double)aq;
         }
+        x = xn;
     }
 }
 
@@ -633,19 +660,20 @@ batched_rts_prefix(Layout L, int64_t B, const double *__restrict__ aggS, const d
 
 template <bool INCL, int V>
 __global__ void __launch_bounds__(kBlock, V <= 4 ? 1 : 3)
-batched_rts_apply(const float *__restrict__ values, const int64_t *__restrict__ off, float *__restrict__ scan_out,
+batched_rts_apply(const float *__restrict__ values, const TileMeta *__restrict__ meta, float *__restrict__ scan_out,
                   Layout L, const double *__restrict__ prefS)
 {
-    constexpr int TILE = kBlock * 4 * V;
     __shared__ float smem[kBlock / 32 + 1];
     __shared__ float s_pre[2];
     const int64_t total = *reinterpret_cast<volatile int64_t *>(L.total_tiles);
     // last tiles first: the sums pass read the values in increasing order, so
     // its most recent tiles are still in L2 when this pass starts
     int par = 0;
+    TileMeta x = blockIdx.x < total ? load_meta(meta, total - 1 - blockIdx.x) : TileMeta{0, 0, 0, 0};
     for (int64_t k = blockIdx.x; k < total; k += gridDim.x, par ^= 1) {   // block-uniform
         const int64_t t = total - 1 - k;
-        const TileInfo x = tile_info<TILE>(t, total, L, off);
+        const int64_t kn = k + gridDim.x;
+        const TileMeta xn = kn < total ? load_meta(meta, total - 1 - kn) : x;   // next placement, in flight
         float v[V][4];
         load_masked<V>(values, x.fbase, x.lo, x.hi, v);
         // one float64 -> float32 conversion per tile, read after the scan's
@@ -654,6 +682,7 @@ batched_rts_apply(const float *__restrict__ values, const int64_t *__restrict__ 
         dev::tile_scan_local<float, INCL, kBlock, V>(v, smem);
         dev::tile_add_prefix<float, V>(v, s_pre[par]);
         store_masked<V>(scan_out, x.fbase, x.lo, x.hi, v);
+        x = xn;
     }
 }
 
@@ -667,16 +696,23 @@ int run_rts(const BatchedLaunch &b, Control *ctl, unsigned char *data, cudaStrea
     double *aggS = reinterpret_cast<double *>(data + layout_bytes(b, TILE));
     double *aggQ = aggS + mt;
     double *prefS = aggQ + mt;
+    // 16-byte loads of the placements: start them on a 256-byte boundary
+    // (3 * 8 * mt bytes of float64 before them is only 8-byte aligned for odd mt)
+    TileMeta *meta = reinterpret_cast<TileMeta *>(data + r256(layout_bytes(b, TILE) + 3 * 8 * (size_t)mt));
     launch_kernel(batched_prep, 1, 1024, 0, s, b.offsets, b.B, b.total, TILE, L, b.results, ctl, mt);
     cudaError_t e = cudaPeekAtLastError();
     if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prep launch");
+    const int64_t mgrid = ceil_div(mt, kBlock) < 4096 ? ceil_div(mt, kBlock) : 4096;
+    launch_kernel(batched_meta<TILE>, (unsigned)mgrid, kBlock, 0, s, b.offsets, L, meta);
+    e = cudaPeekAtLastError();
+    if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched meta launch");
     int64_t grid = mt;
     const int64_t cap = (int64_t)device_info().sms * 64;
     if (grid > cap) grid = cap;
     const bool sc = b.want_scan, rd = b.want_reduce;
-    if (sc && rd) launch_kernel(batched_rts_sums<true, true, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, L, aggS, aggQ);
-    else if (sc) launch_kernel(batched_rts_sums<true, false, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, L, aggS, aggQ);
-    else launch_kernel(batched_rts_sums<false, true, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, L, aggS, aggQ);
+    if (sc && rd) launch_kernel(batched_rts_sums<true, true, V>, (unsigned)grid, kBlock, 0, s, b.values, meta, L, aggS, aggQ);
+    else if (sc) launch_kernel(batched_rts_sums<true, false, V>, (unsigned)grid, kBlock, 0, s, b.values, meta, L, aggS, aggQ);
+    else launch_kernel(batched_rts_sums<false, true, V>, (unsigned)grid, kBlock, 0, s, b.values, meta, L, aggS, aggQ);
     e = cudaPeekAtLastError();
     if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched sums launch");
     const int64_t pgrid = ceil_div(b.B, kBlock / 32) < 4096 ? ceil_div(b.B, kBlock / 32) : 4096;
@@ -685,8 +721,8 @@ int run_rts(const BatchedLaunch &b, Control *ctl, unsigned char *data, cudaStrea
     e = cudaPeekAtLastError();
     if (e != cudaSuccess) return fail_cuda(cudaGetLastError(), "batched prefix launch");
     if (!sc) return SKEL_OK;
-    if (b.inclusive) launch_kernel(batched_rts_apply<true, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.scan_out, L, prefS);
-    else launch_kernel(batched_rts_apply<false, V>, (unsigned)grid, kBlock, 0, s, b.values, b.offsets, b.scan_out, L, prefS);
+    if (b.inclusive) launch_kernel(batched_rts_apply<true, V>, (unsigned)grid, kBlock, 0, s, b.values, meta, b.scan_out, L, prefS);
+    else launch_kernel(batched_rts_apply<false, V>, (unsigned)grid, kBlock, 0, s, b.values, meta, b.scan_out, L, prefS);
     e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "batched apply launch");
 }
@@ -700,12 +736,15 @@ const char *batched_variant_name(int v)
                                   "persistent_warp_lookback", "reduce_then_scan"};
     return v >= 0 && v < 6 ? names[v] : "?";
 }
-Choice batched_default() { return Choice{5, 256, 4, 0}; }
+Choice batched_default() { return Choice{5, 256, 8, 0}; }
 
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c)
 {
-    // reduce-then-scan also keeps three float64 values per tile
-    return layout_bytes(b, tile_of(c)) + (c.variant == 5 ? 3 * 8 * (size_t)max_tiles(b, tile_of(c)) : 0);
+    // reduce-then-scan also keeps three float64 values per tile and, from the
+    // next 256-byte boundary, a 32-byte placement per tile
+    if (c.variant != 5) return layout_bytes(b, tile_of(c));
+    const size_t mt = (size_t)max_tiles(b, tile_of(c));
+    return r256(layout_bytes(b, tile_of(c)) + 3 * 8 * mt) + 32 * mt;
 }
 // aggregate and prefix of every tile, two words (scan carry, sum of squares) each
 size_t batched_word_count(const BatchedLaunch &b, const Choice &c) { return 4 * (size_t)max_tiles(b, tile_of(c)); }
