@@ -479,6 +479,119 @@ def coulomb_leg(sk, torch, stream, clocks, reps: int = 5):
             "variant": list(sk.skel_last_variant("maparray"))}
 
 
+# ----------------------------------------- the other workload configurations --
+def _event_ms(torch, stream, fn, reps):
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def config_legs(sk, torch, stream):
+    """Measurements of the other workload configurations, reported apart
+    from the step: dot at n = 2^20 (latency-bound, cold and warm L2), a
+    10-call 9-point stencil chain on 8192^2 (composed vs one call per step),
+    the batched instances as one CUDA-graph replay against 2 x 4096 separate
+    calls, and forward + backward of the composed loss on 8192^2."""
+    dev = torch.device("cuda")
+    out = {}
+    # dot, n = 2^20
+    n = 1 << 20
+    x = torch.from_numpy(syn.uniform_f32(syn.SEED_X, n)).to(dev)
+    y = torch.from_numpy(syn.uniform_f32(syn.SEED_Y, n)).to(dev)
+    r = torch.zeros(1, device=dev)
+    cx, cy, cr = (sk.Container.from_tensor(t) for t in (x, y, r))
+    dot = lambda: sk.skel_mapreduce("mul", "add", [cx, cy], cr, host=False)
+    for _ in range(3):
+        dot()
+    # warm: 20 calls back to back on the device (a sleep kernel ahead of them
+    # covers the host's time to enqueue them)
+    torch.cuda._sleep(4_000_000)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        dot()
+    e1.record(stream)
+    e1.synchronize()
+    warm = e0.elapsed_time(e1) / 20
+    flush = torch.empty(1 << 28, dtype=torch.float32, device=dev)
+    cold = []
+    for _ in range(10):
+        flush.sum()                                   # evict the operands from L2
+        cold.append(_event_ms(torch, stream, dot, 1))
+    out["dot_2e20"] = {"us_warm": round(warm * 1e3, 2), "us_cold": round(statistics.median(cold) * 1e3, 2),
+                       "GB/s_warm": round(8 * n / (warm * 1e-3) / 1e9, 1),
+                       "GB/s_cold": round(8 * n / (statistics.median(cold) * 1e-3) / 1e9, 1)}
+    del flush
+    # 10-step 9-point chain, 8192^2
+    side, steps = 8192, 10
+    g = torch.from_numpy(syn.uniform_f32(syn.SEED_GRID, side * side, 0.0, 1.0).reshape(side, side)).to(dev)
+    o, t = torch.empty_like(g), torch.empty_like(g)
+    cg, co, ct = (sk.Container.from_tensor(v) for v in (g, o, t))
+    chain = lambda: sk.skel_mapoverlap_chain("stencil9", None, "clamp", steps, cg, ct, co)
+    chain()
+    ms_chain = _event_ms(torch, stream, chain, 5)
+    variant = list(sk.skel_last_variant("chain2d"))
+
+    def per_call():
+        src = cg
+        for k in range(steps):
+            dst = co if (steps - 1 - k) % 2 == 0 else ct
+            sk.skel_mapoverlap("stencil9", 1, None, "clamp", src, dst)
+            src = dst
+    per_call()
+    ms_calls = _event_ms(torch, stream, per_call, 5)
+    out["chain_9pt_8192sq_x10"] = {"ms_composed": round(ms_chain, 3), "ms_per_call": round(ms_calls, 3),
+                                   "speedup": round(ms_calls / ms_chain, 3), "variant": variant,
+                                   "GB/s_equivalent": round(8 * side * side * steps / (ms_chain * 1e-3) / 1e9, 1)}
+    for c in (cg, co, ct):
+        c.close()
+    # batched: graph replay against per-instance calls
+    lens = syn.loguniform_lengths(syn.SEED_BATCH_LEN, BATCH_B)
+    off = syn.csr_offsets(lens)
+    total = int(off[-1])
+    bv = torch.from_numpy(syn.uniform_f32(syn.SEED_BATCH_VAL, total)).to(dev)
+    boff = torch.from_numpy(off).to(dev)
+    bres, bsc = torch.empty(BATCH_B, device=dev), torch.empty(total, device=dev)
+    cv, cof, cre, csc = (sk.Container.from_tensor(v) for v in (bv, boff, bres, bsc))
+    plan = sk.Plan(cv, cof, cre, csc, True)
+    plan.launch()
+    ms_graph = _event_ms(torch, stream, plan.launch, 5)
+    views = [(cv.view(int(off[b]), (int(lens[b]),)), csc.view(int(off[b]), (int(lens[b]),)),
+              cre.view(b, (1,))) for b in range(BATCH_B) if lens[b] > 0]
+
+    def separate():
+        for v, sv, rv in views:
+            sk.skel_mapreduce("sq", "add", [v], rv, host=False)
+            sk.skel_scan("add", True, v, sv)
+    separate()
+    ms_sep = _event_ms(torch, stream, separate, 2)
+    out["batched_4096"] = {"ms_graph": round(ms_graph, 3), "ms_separate_calls": round(ms_sep, 3),
+                           "speedup": round(ms_sep / ms_graph, 2), "calls_separate": 2 * len(views)}
+    for v, sv, rv in views:
+        v.close(); sv.close(); rv.close()
+    plan.close()
+    for c in (cv, cof, cre, csc):
+        c.close()
+    # composed loss forward + backward, 8192^2
+    from paper_1405_2915_gb300.autograd import composed_loss
+    xg = torch.from_numpy(syn.uniform_f32(syn.SEED_GRAD, side * side).reshape(side, side)).to(dev)
+    xg.requires_grad_(True)
+
+    def fwd_bwd():
+        xg.grad = None
+        composed_loss(xg).backward()
+    fwd_bwd()
+    ms_ad = _event_ms(torch, stream, fwd_bwd, 5)
+    out["autograd_8192sq"] = {"ms_fwd_bwd": round(ms_ad, 3)}
+    return out
+
+
 # -------------------------------------------------------------------- main --
 def main():
     ap = argparse.ArgumentParser()
@@ -602,6 +715,7 @@ def main():
     torch.cuda.empty_cache()
     if not args.only and not args.force and not args.no_next:
         line["next"] = {"coulomb_grid": coulomb_leg(sk, torch, stream, clocks)}
+        line["configs"] = config_legs(sk, torch, stream)
     if not args.no_e2e:
         dt, h2d, d2h, cpus, per_step = e2e_run(sk, torch, min(args.steps, 5), stream)
         dt = max_over_ranks(dt * 1e3) / 1e3

@@ -640,7 +640,10 @@ int skel_scan(skel_fn op, int inclusive, skel_handle in, skel_handle out, void *
         if (rc) return rc;
         ScanLaunch sc{in->dtype, inclusive != 0, false, ops[0].ptr, ops[1].ptr, in->n,
                       in->ndim == 2 ? in->shape[1] : 0};
-        Context ctx{SKEL_SK_SCAN, inclusive ? 1 : 0, in->dtype, in->ndim == 2 ? in->shape[1] : in->n, 0, res};
+        // keyed by the total element count: the variants scan all rows in one
+        // launch, so the work, not the row length, decides which is fastest
+        // (a row length of 8192 once picked the one-block variant for 8192 rows)
+        Context ctx{SKEL_SK_SCAN, inclusive ? 1 : 0, in->dtype, in->n, 0, res};
         return run_with_fallback(SKEL_SK_SCAN, ctx, [&](const Choice &c) { return launch_scan(sc, c, s); }, scan_def);
     });
 }
@@ -1069,7 +1072,7 @@ int skel_scan_bwd(skel_fn op, int inclusive, skel_handle gout, skel_handle gin, 
         ScanLaunch sc{SKEL_F32, inclusive != 0, true, ops[0].ptr, ops[1].ptr, gout->n,
                       gout->ndim == 2 ? gout->shape[1] : 0};
         // reverse scans have their own keys (fn 2: exclusive, 3: inclusive)
-        Context ctx{SKEL_SK_SCAN, inclusive ? 3 : 2, SKEL_F32, gout->ndim == 2 ? gout->shape[1] : gout->n, 0, res};
+        Context ctx{SKEL_SK_SCAN, inclusive ? 3 : 2, SKEL_F32, gout->n, 0, res};   // total work, as forward
         return run_with_fallback(SKEL_SK_SCAN, ctx, [&](const Choice &c) { return launch_scan(sc, c, s); }, scan_def);
     });
 }
