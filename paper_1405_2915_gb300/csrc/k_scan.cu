@@ -27,6 +27,12 @@
 //                       the aggregate before the in-place scans (16-byte
 //                       aligned operands; reverse and row-wise scans need
 //                       segments of a multiple of 4 elements).
+//   6 lookback_ws       one persistent block per SM split into producer,
+//                       scanner, look-back and store warps that pass tiles
+//                       through a ring of staged tiles (tile=0: four 48 KiB
+//                       stages, 1: six 32 KiB stages), so a tile's look-back
+//                       overlaps the copies, scans and stores of its
+//                       neighbours (same operand rules as variant 5).
 // ept selects V, the 16-byte groups per thread (tile = 256 threads x 4V).
 // float32: element arithmetic is float32; the prefix carried from tile to
 // tile is float64 (one add per tile), rounded to float32 once per tile.
@@ -141,6 +147,19 @@ __device__ __forceinline__ uint32_t mbar_try(const uint64_t *bar, uint32_t parit
                  : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return done;
 }
+
+// As mbar_try, but a thread whose phase is not complete is suspended until
+// it completes or about hint_ns pass (instead of the short default limit),
+// so waiting threads leave the shared-memory pipe and the issue slots to the
+// warps that work.
+__device__ __forceinline__ uint32_t mbar_try_sleep(const uint64_t *bar, uint32_t parity, uint32_t hint_ns)
+{
+    uint32_t done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns) : "memory");
+    return done;
+}
+constexpr uint32_t kSleepHintNs = 20000;   // 20 us per suspended try
 
 // Thread 0: draws the next ticket for stage s and starts its copy.
 template <class T>
@@ -493,6 +512,483 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
     }
 }
 
+// ------------------------------------ variant 6: warp-specialised stages --
+// One persistent block per SM whose warps split into four roles; a tile
+// moves through them in a ring of shared-memory stages, each hand-over an
+// mbarrier phase:
+//   producer  (warp 0, one thread): draws tickets in order and starts the bulk
+//             copies of each drawn tile into the next free stage (full[s]);
+//   reducers  (4 warps): sum the tile's eight chunks, publish the tile
+//             aggregate at once (reduced[s]);
+//   look-back (8 warps): walk the tile's predecessors, 512 per round, publish
+//             its inclusive prefix and give each chunk its prefix
+//             (prefixed[s]);
+//   scanners  (8 warps, one chunk each): scan the chunk with warp scans in
+//             registers, add the prefix and store it, then free the stage
+//             (empty[s]).
+// A block that runs the phases one after another (variant 5) holds each tile
+// through its look-back round trip and its stores while no copy is in
+// flight.  Here the look-back of tile i overlaps the reduction of tile i+1,
+// the scans and stores of tile i-1 and the copies of the tiles after them.
+// The scan itself needs no block barrier: a chunk's prefix (the tile prefix
+// plus the sums of the chunks before it) is known before its warp starts.
+//
+// The look-back rounds are twice as wide as variant 5's because the blocks
+// move in step: the predecessors drawn in the same round of tickets (one per
+// block) are still walking, and their inclusive prefixes appear about when
+// this walk starts; 512 predecessors reach back past them to tiles published
+// a whole period earlier, so a walk usually ends after one round trip.
+//
+// Progress: tickets are drawn in order and every role takes its block's
+// tiles in that order, so the smallest unfinished tile has all of its
+// predecessors finished and each of its roles free to take it.  Every wait
+// is bounded (globaltimer); a wait that runs out records kErrTimeout and
+// sets the block's abort word, which ends the other roles' waits; before
+// the block leaves, the producer waits (bounded) for each copy it issued.
+constexpr int kWsRedW = 4, kWsLookW = 8, kWsScanW = 8;
+constexpr int kWsThreads = 32 * (1 + kWsRedW + kWsLookW + kWsScanW);   // 672
+constexpr int kWsChunks = kWsScanW;                                    // chunks per tile
+constexpr int kWsLookE = 2;                                            // windows per look-back lane
+constexpr int kWsBarRed = 1, kWsBarLook = 2, kWsBarScan = 3;           // named barriers (0: __syncthreads)
+
+__device__ __forceinline__ void mbar_init_count(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void group_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" :: "r"(id), "r"(nthreads) : "memory");
+}
+// Barrier over one role's threads that also ANDs a predicate across them.
+__device__ __forceinline__ bool group_and(int id, int nthreads, bool p)
+{
+    uint32_t r;
+    asm volatile("{ .reg .pred pi, po; setp.ne.u32 pi, %1, 0; bar.red.and.pred po, %2, %3, pi; selp.u32 %0, 1, 0, po; }"
+                 : "=r"(r) : "r"((uint32_t)p), "r"(id), "r"(nthreads) : "memory");
+    return r != 0;
+}
+
+// Bounded wait for the phase of parity par; false when it ran out or the
+// block's abort word was set.
+__device__ __forceinline__ bool ws_wait(const uint64_t *bar, uint32_t par, const volatile int *abort_word,
+                                        uint64_t limit_ns)
+{
+    const uint64_t t0 = dev::globaltimer();
+    for (uint32_t k = 0; k < (1u << 26); ++k) {
+        if (mbar_try_sleep(bar, par, kSleepHintNs)) return true;
+        if (*abort_word || dev::globaltimer() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// The wide look-back walk run by one role of NW warps, each lane polling NE
+// predecessors per round: window k (k = w + NW*e, 32 predecessors) holds
+// pred - 32k - lane, so the windows are numbered by distance.  A warp polls
+// until its windows are ready up to its nearest inclusive prefix; warp 0
+// then adds windows 0..kmax (kmax: the nearest window holding a published
+// prefix).  The aggregate (and a segment's first inclusive prefix) was
+// published by the reducers.
+template <class CT, int NW, int NE>
+__device__ __forceinline__ CT group_lookback(int64_t tile, int64_t first, CT agg, LookbackDesc d, uint32_t epoch,
+                                             Control *ctl, uint64_t limit_ns, bool pub_incl,
+                                             dev::WideLookbackSmem<CT, NW * NE> &sm, int w, int lane, int id)
+{
+    constexpr int W = dev::Codec<CT>::W;
+    if (tile == first) return CT(0);
+    CT excl = CT(0);
+    int64_t pred = tile - 1;
+    uint64_t t0 = 0;
+    bool gave_up = false;
+    while (true) {
+        uint32_t status[NE];
+        unsigned incl_mask[NE];
+        CT val[NE];
+        while (true) {
+            bool ok = true, seen_incl = false;
+            // every poll of the round is in flight before any is looked at
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const int64_t p = pred - 32 * (w + NW * e) - lane;
+                if (p >= first) status[e] = dev::peek<CT>(d, p, epoch, val[e]);
+                else { status[e] = dev::kStIncl; val[e] = CT(0); }   // before the segment start: prefix 0
+            }
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+                const unsigned ready_mask = __ballot_sync(0xffffffffu, status[e] != 0);
+                incl_mask[e] = __ballot_sync(0xffffffffu, status[e] == dev::kStIncl);
+                const unsigned need = incl_mask[e] ? (((incl_mask[e] & (0u - incl_mask[e])) << 1) - 1u) : 0xffffffffu;
+                if (!seen_incl) ok = ok && (ready_mask & need) == need;   // windows past this warp's first prefix do not count
+                seen_incl = seen_incl || incl_mask[e] != 0u;
+            }
+            if (ok || gave_up) break;
+            if (t0 == 0) t0 = dev::globaltimer();
+            bool expired = (dev::globaltimer() - t0 > limit_ns) || dev::ld_volatile(&ctl->abort) == epoch;
+            expired = __any_sync(0xffffffffu, expired);
+            if (expired) {
+                if (lane == 0) {
+                    atomicOr(&ctl->error, kErrTimeout);
+                    atomicExch(&ctl->abort, epoch);
+                }
+                gave_up = true;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+            const unsigned lim = incl_mask[e] ? (((incl_mask[e] & (0u - incl_mask[e])) << 1) - 1u) : 0xffffffffu;
+            CT v = val[e];
+            if (!((lim >> lane) & 1u) || status[e] == 0) v = CT(0);
+            sm.vals[(w + NW * e) * 32 + lane] = v;
+            if (lane == 0) sm.incl[w + NW * e] = incl_mask[e] != 0u;
+        }
+        group_sync(id, NW * 32);
+        if (w == 0) {
+            int kmax = NW * NE - 1;
+            bool found_any = false;
+#pragma unroll
+            for (int k = NW * NE - 1; k >= 0; --k)
+                if (sm.incl[k]) { kmax = k; found_any = true; }
+            CT wv[NW * NE];   // all loads in flight at once, then a pairwise sum
+#pragma unroll
+            for (int k = 0; k < NW * NE; ++k) wv[k] = k <= kmax ? sm.vals[k * 32 + lane] : CT(0);
+#pragma unroll
+            for (int st = 1; st < NW * NE; st *= 2)
+#pragma unroll
+                for (int k = 0; k + st < NW * NE; k += 2 * st) wv[k] = wv[k] + wv[k + st];
+            CT acc = wv[0];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc = acc + dev::shfl_xor_ct(acc, o);
+            if (lane == 0) {
+                sm.total = excl + acc;
+                sm.found = found_any;
+            }
+        }
+        group_sync(id, NW * 32);
+        excl = sm.total;
+        const bool found = sm.found;
+        group_sync(id, NW * 32);   // sm is rewritten by the next round
+        if (found) break;
+        pred -= 32 * NW * NE;
+    }
+    if (pub_incl && w == 0 && lane == 0) dev::Codec<CT>::put(d.incl + tile * W, excl + agg, epoch);
+    return excl;
+}
+
+template <class T, bool INCL, bool REV, int SUB, int STAGES>
+__global__ void __launch_bounds__(kWsThreads, 1)
+scan_ws(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc d, Control *ctl, uint32_t epoch,
+        int64_t skip_tile, uint64_t limit_ns)
+{
+    using CT = typename ScanTypes<T>::CT;
+    using V4 = typename ScanTypes<T>::V4;
+    using AddOp = typename std::conditional<std::is_same<T, float>::value, dev::AddF, dev::AddU>::type;
+    constexpr int TILE = SUB * kTmaTile;
+    constexpr int CH = TILE / kWsChunks;   // elements per chunk (a multiple of 512)
+    constexpr int KS = CH / 128;           // 16-byte groups per lane in a chunk
+    constexpr int W = dev::Codec<CT>::W;
+    static_assert(CH % 512 == 0, "chunks are scanned four 128-element steps at a time");
+    extern __shared__ __align__(1024) unsigned char dyn[];   // STAGES tiles
+    __shared__ __align__(8) uint64_t full[STAGES], reduced[STAGES], prefixed[STAGES], empty[STAGES];
+    __shared__ int64_t tile_of[STAGES];
+    __shared__ CT agg_of[STAGES];
+    __shared__ CT cpre_of[STAGES][kWsChunks];   // exclusive prefix of the chunk sums
+    __shared__ T pre_of[STAGES][kWsChunks];     // each chunk's prefix, in element type
+    __shared__ T csum[kWsChunks];
+    __shared__ dev::WideLookbackSmem<CT, kWsLookW * kWsLookE> lbs;
+    __shared__ int abort_word;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init_count(&full[s], 1);
+            mbar_init_count(&reduced[s], 1);
+            mbar_init_count(&prefixed[s], 1);
+            mbar_init_count(&empty[s], 1);
+        }
+        abort_word = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();   // the last block-wide barrier: the roles part here
+    volatile int *abort_v = &abort_word;
+    auto stage = [&](int s) { return reinterpret_cast<T *>(dyn + (size_t)s * TILE * sizeof(T)); };
+    auto give_up = [&]() {
+        *abort_v = 1;
+        atomicOr(&ctl->error, kErrTimeout);
+    };
+    // Input values of logical elements e..e+3 of a staged tile of len
+    // elements: slot e forward, len-1-e reverse (reverse tiles have
+    // len % 4 == 0); the unstaged forward tail (len % 4 elements) is read
+    // from global memory.
+    auto src4 = [&](const T *buf, const TileMap &m, int64_t e, T (&a)[4]) {
+        const int64_t len = m.len, whole = len & ~(int64_t)3;
+        if (e + 3 < whole) {
+            const V4 q = *reinterpret_cast<const V4 *>(buf + (REV ? len - 4 - e : e));
+            if (!REV) { a[0] = q.x; a[1] = q.y; a[2] = q.z; a[3] = q.w; }
+            else      { a[0] = q.w; a[1] = q.z; a[2] = q.y; a[3] = q.x; }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                a[u] = e + u < whole ? buf[REV ? len - 1 - e - u : e + u] : (e + u < len ? in[m.base + e + u] : T(0));
+        }
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------------ producer --
+        if (lane != 0) return;
+        uint32_t last_par[STAGES];
+        bool used[STAGES];
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) used[s] = false;
+        for (uint32_t i = 0;; ++i) {
+            const int s = (int)(i % STAGES);
+            if (i >= STAGES && !ws_wait(&empty[s], ((i / STAGES) - 1u) & 1u, abort_v, limit_ns)) {
+                give_up();
+                break;
+            }
+            const int64_t t = (int64_t)atomicAdd(&ctl->ticket, 1u);
+            tile_of[s] = t;
+            used[s] = true;
+            last_par[s] = (i / STAGES) & 1u;
+            if (t >= g.ntiles) {   // the end marker: a phase with no bytes
+                mbar_arrive(&full[s]);
+                break;
+            }
+            int64_t first;
+            const TileMap m = tile_map<TILE>(g, t, &first);
+            const int64_t pstart = m.rev ? m.base - (m.len - 1) : m.base;
+            const uint32_t bytes = (uint32_t)((m.len * (int64_t)sizeof(T)) & ~(int64_t)15);
+            const uint32_t bar = smem_u32(&full[s]);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the scanners' reads before the refill
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+            for (uint32_t o = 0; o < bytes; o += 16384u) {
+                const uint32_t sz = bytes - o < 16384u ? bytes - o : 16384u;
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             :: "r"(smem_u32(reinterpret_cast<unsigned char *>(stage(s)) + o)),
+                                "l"(reinterpret_cast<const unsigned char *>(in + pstart) + o), "r"(sz), "r"(bar)
+                             : "memory");
+            }
+        }
+        // every block has drawn its last ticket once the count reaches the grid
+        if (atomicAdd(&ctl->exited, 1u) == gridDim.x - 1) {
+            ctl->ticket = 0u;
+            ctl->exited = 0u;
+        }
+        // no copy may land after the block has left: wait (bounded) for the
+        // last phase issued on each stage (at once unless a role gave up)
+#pragma unroll
+        for (int s = 0; s < STAGES; ++s) {
+            if (!used[s]) continue;
+            uint32_t ok = 0;
+            for (uint32_t k = 0; k < (1u << 22) && !ok; ++k) ok = mbar_try(&full[s], last_par[s]);
+        }
+        return;
+    }
+
+    if (warp <= kWsRedW) {
+        // ------------------------------------------------------ reducers --
+        // warp r sums chunks r and r + kWsRedW: pairwise within each lane,
+        // then a warp tree; the leader adds the chunk sums in order.
+        const int r = warp - 1, gt = threadIdx.x - 32;
+        constexpr int kN = kWsRedW * 32;
+        for (uint32_t i = 0;; ++i) {
+            const int s = (int)(i % STAGES);
+            if (!group_and(kWsBarRed, kN, ws_wait(&full[s], (i / STAGES) & 1u, abort_v, limit_ns))) {
+                if (gt == 0) give_up();
+                return;
+            }
+            const int64_t tile = tile_of[s];
+            if (tile >= g.ntiles) {
+                if (gt == 0) mbar_arrive(&reduced[s]);
+                return;
+            }
+            int64_t first;
+            const TileMap m = tile_map<TILE>(g, tile, &first);
+            const T *buf = stage(s);
+#pragma unroll 1
+            for (int cc = 0; cc < kWsChunks / kWsRedW; ++cc) {
+                const int c = r + kWsRedW * cc;
+                // four running sums of pairwise groups, then a pairwise finish
+                T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 1
+                for (int k0 = 0; k0 < KS; k0 += 4) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        T a[4];
+                        src4(buf, m, (int64_t)c * CH + (k0 + k) * 128 + lane * 4, a);
+                        acc[k] = acc[k] + ((a[0] + a[1]) + (a[2] + a[3]));
+                    }
+                }
+                const T cs = dev::warp_reduce<AddOp>((acc[0] + acc[1]) + (acc[2] + acc[3]));
+                if (lane == 0) csum[c] = cs;
+            }
+            group_sync(kWsBarRed, kN);
+            if (gt == 0) {
+                CT run = CT(0);
+#pragma unroll
+                for (int c = 0; c < kWsChunks; ++c) {
+                    cpre_of[s][c] = run;
+                    run = run + (CT)csum[c];
+                }
+                agg_of[s] = run;
+                if (tile != skip_tile) {
+                    if (tile == first) dev::Codec<CT>::put(d.incl + tile * W, run, epoch);
+                    else dev::Codec<CT>::put(d.agg + tile * W, run, epoch);
+                }
+                mbar_arrive(&reduced[s]);
+            }
+            group_sync(kWsBarRed, kN);   // csum is rewritten by the next tile
+        }
+    }
+
+    if (warp <= kWsRedW + kWsLookW) {
+        // ----------------------------------------------------- look-back --
+        const int w = warp - 1 - kWsRedW, gt = threadIdx.x - 32 * (1 + kWsRedW);
+        constexpr int kN = kWsLookW * 32;
+        for (uint32_t i = 0;; ++i) {
+            const int s = (int)(i % STAGES);
+            if (!group_and(kWsBarLook, kN, ws_wait(&reduced[s], (i / STAGES) & 1u, abort_v, limit_ns))) {
+                if (gt == 0) give_up();
+                return;
+            }
+            const int64_t tile = tile_of[s];
+            if (tile >= g.ntiles) {
+                if (gt == 0) mbar_arrive(&prefixed[s]);
+                return;
+            }
+            int64_t first;
+            (void)tile_map<TILE>(g, tile, &first);
+            const CT agg = agg_of[s];
+            const CT p = group_lookback<CT, kWsLookW, kWsLookE>(tile, first, agg, d, epoch, ctl, limit_ns,
+                                                                tile != skip_tile, lbs, w, lane, kWsBarLook);
+            if (gt == 0) {
+#pragma unroll
+                for (int c = 0; c < kWsChunks; ++c) pre_of[s][c] = dev::to_elem<T>(p + cpre_of[s][c]);
+                mbar_arrive(&prefixed[s]);
+            }
+        }
+    }
+
+    {
+        // ------------------------------------------------------ scanners --
+        // warp c scans chunk c in steps of 128 elements (4 per lane): an
+        // in-thread scan of 4, a warp scan of the lane totals, a running
+        // chunk-local carry; the chunk prefix is added last, once per element.
+        const int c = warp - 1 - kWsRedW - kWsLookW, gt = threadIdx.x - 32 * (1 + kWsRedW + kWsLookW);
+        constexpr int kN = kWsScanW * 32;
+        for (uint32_t i = 0;; ++i) {
+            const int s = (int)(i % STAGES);
+            const uint32_t par = (i / STAGES) & 1u;
+            // the full wait (complete already) makes the staged bytes visible here directly
+            if (!group_and(kWsBarScan, kN, ws_wait(&prefixed[s], par, abort_v, limit_ns) &&
+                                           ws_wait(&full[s], par, abort_v, limit_ns))) {
+                if (gt == 0) give_up();
+                return;
+            }
+            const int64_t tile = tile_of[s];
+            if (tile >= g.ntiles) return;
+            int64_t first;
+            const TileMap m = tile_map<TILE>(g, tile, &first);
+            const int64_t len = m.len;
+            const int64_t pstart = m.rev ? m.base - (len - 1) : m.base;
+            const T *buf = stage(s);
+            const T pre = pre_of[s][c];
+            T carry = T(0);
+#pragma unroll 1
+            for (int k0 = 0; k0 < KS; k0 += 4) {
+                T v[4][4];
+                T lex[4], wtot[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    src4(buf, m, (int64_t)c * CH + (k0 + k) * 128 + lane * 4, v[k]);
+                    v[k][1] = v[k][0] + v[k][1];
+                    v[k][2] = v[k][1] + v[k][2];
+                    v[k][3] = v[k][2] + v[k][3];
+                    const T wi = dev::warp_incl_scan_add(v[k][3]);
+                    T x = __shfl_up_sync(0xffffffffu, wi, 1);
+                    lex[k] = lane == 0 ? T(0) : x;
+                    wtot[k] = __shfl_sync(0xffffffffu, wi, 31);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const T b = carry + lex[k];
+                    carry = carry + wtot[k];
+                    T o[4];
+                    if (INCL) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) o[u] = pre + (b + v[k][u]);
+                    } else {
+                        o[0] = pre + b;
+#pragma unroll
+                        for (int u = 1; u < 4; ++u) o[u] = pre + (b + v[k][u - 1]);
+                    }
+                    const int64_t e = (int64_t)c * CH + (k0 + k) * 128 + lane * 4;   // logical
+                    if (e + 3 < len) {
+                        V4 q;
+                        if (!REV) { q.x = o[0]; q.y = o[1]; q.z = o[2]; q.w = o[3]; }
+                        else      { q.x = o[3]; q.y = o[2]; q.z = o[1]; q.w = o[0]; }
+                        dev::st_stream(reinterpret_cast<V4 *>(out + pstart + (REV ? len - 4 - e : e)), q);
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u)
+                            if (e + u < len) out[pstart + (REV ? len - 1 - e - u : e + u)] = o[u];
+                    }
+                }
+            }
+            group_sync(kWsBarScan, kN);   // every scanner has read the stage
+            if (gt == 0) mbar_arrive(&empty[s]);
+        }
+    }
+}
+
+template <class T, bool INCL, bool REV, int SUB, int STAGES>
+int launch_scan_ws(const ScanLaunch &sc, cudaStream_t s)
+{
+    const T *in = static_cast<const T *>(sc.in);
+    T *out = static_cast<T *>(sc.out);
+    constexpr int TILE = SUB * kTmaTile;
+    SegGeom g;
+    g.seglen = sc.seg > 0 ? sc.seg : sc.n;
+    g.tps = ceil_div(g.seglen, TILE);
+    g.ntiles = g.tps * (sc.n / g.seglen);
+    g.rev = REV;
+    g.vec_ok = true;
+    if (g.ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
+    auto kern = scan_ws<T, INCL, REV, SUB, STAGES>;
+    const int dyn = STAGES * TILE * (int)sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return fail_cuda(e, "scan ws: shared memory opt-in");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kWsThreads, dyn);
+    if (e != cudaSuccess || occ < 1) return fail(SKEL_ERR_UNSUPPORTED, "scan ws: kernel does not fit an SM");
+    int64_t grid = (int64_t)device_info().sms * occ;
+    if (grid > g.ntiles) grid = g.ntiles;
+    Scratch scr{};
+    int rc = get_scratch(s, 0, 2 * (size_t)g.ntiles, &scr);
+    if (rc) return rc;
+    LookbackDesc d{scr.words, scr.words + g.ntiles};
+    const DebugKnobs k = debug_knobs();
+    launch_kernel(kern, (unsigned)grid, kWsThreads, (size_t)dyn, s, in, out, g, d, scr.ctl, scr.epoch,
+                  k.scan_skip_publish_tile, k.wait_limit_ns);
+    e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan ws launch");
+}
+
+// tile: 0 selects 48 KiB tiles in four stages, 1 selects 32 KiB tiles in six.
+template <class T, bool INCL>
+int run_scan_ws(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+{
+    if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan ws: ept must be 4");
+    if (c.tile < 0 || c.tile > 1) return fail(SKEL_ERR_INVALID_ARG, "scan ws: tile must be 0 or 1");
+    const int64_t seglen = sc.seg > 0 ? sc.seg : sc.n;
+    if (!aligned16(sc.in) || !aligned16(sc.out) || ((sc.seg > 0 || sc.reverse) && seglen % 4))
+        return fail(SKEL_ERR_UNSUPPORTED, "scan ws: 16-byte aligned operands and segments needed");
+    if (sc.reverse)
+        return c.tile ? launch_scan_ws<T, INCL, true, 2, 6>(sc, s) : launch_scan_ws<T, INCL, true, 3, 4>(sc, s);
+    return c.tile ? launch_scan_ws<T, INCL, false, 2, 6>(sc, s) : launch_scan_ws<T, INCL, false, 3, 4>(sc, s);
+}
+
 // Variant 0, kernel 1: per-tile aggregate (the tile is scanned to obtain it
 // in the same order the apply kernel uses).
 template <class T, int V>
@@ -724,6 +1220,7 @@ int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (c.variant == 4) return run_scan_tma<T, INCL>(sc, c, s);
     if (c.variant == 5) return run_scan_big<T, INCL>(sc, c, s);
+    if (c.variant == 6) return run_scan_ws<T, INCL>(sc, c, s);
     const int v = c.ept > 0 ? c.ept : 4;
     switch (v) {
     case 2: return run_scan<T, INCL, 2>(sc, c, s);
@@ -735,19 +1232,19 @@ int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 
 }  // namespace
 
-int scan_variant_count() { return 6; }
+int scan_variant_count() { return 7; }
 const char *scan_variant_name(int v)
 {
     static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block", "lookback_tma",
-                                  "lookback_big"};
-    return v >= 0 && v < 6 ? names[v] : "?";
+                                  "lookback_big", "lookback_ws"};
+    return v >= 0 && v < 7 ? names[v] : "?";
 }
 Choice scan_default() { return Choice{0, 256, 4, 0}; }
 
 int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (sc.n == 0) return SKEL_OK;
-    if (c.variant < 0 || c.variant > 5) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
+    if (c.variant < 0 || c.variant > 6) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "scan: block must be 256");
     if (sc.seg > 0 && sc.n % sc.seg) return fail(SKEL_ERR_SHAPE, "scan: n is not a multiple of the segment");
     if (sc.dtype == SKEL_F32)

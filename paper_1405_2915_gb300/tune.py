@@ -86,6 +86,8 @@ def candidates(sk_name: str):
         yield (4, 256, 4, 0)
         for t in (0, 1, 2, 3):   # early aggregate (bit 0), 48 KiB tiles (bit 1)
             yield (5, 256, 4, t)
+        for t in (0, 1):         # warp-specialised stages: 4 x 48 KiB, 6 x 32 KiB
+            yield (6, 256, 4, t)
     elif sk_name == "mapoverlap2d":
         yield (0, 256, 0, 0)
         yield (1, 256, 0, 0)

@@ -144,28 +144,30 @@ def test_composed_loss_8192_fd_and_oracle_gradient():
 
 @pytest.mark.parametrize("n", [4, 4096, 12288, 12292, 16384, 16388, 1_000_000, 1 << 22])
 @pytest.mark.parametrize("inclusive", [True, False])
-@pytest.mark.parametrize("tile", [0, 1, 3])
-def test_scan_bwd_big_tiles(n, inclusive, tile):
-    """Reverse scans through the staged big-tile variant (n % 4 == 0)."""
+@pytest.mark.parametrize("variant,tile", [(5, 0), (5, 1), (5, 3), (6, 0), (6, 1)])
+def test_scan_bwd_big_tiles(n, inclusive, variant, tile):
+    """Reverse scans through the staged big-tile and warp-specialised
+    variants (n % 4 == 0)."""
     import torch
     from helpers import forced
     sk = skel()
     g = syn.uniform_f32(10, n)
     out = dev_empty((n,), torch.float32)
-    with forced("scan", 5, 0, 0, tile):
+    with forced("scan", variant, 0, 0, tile):
         sk.skel_scan_bwd("add", inclusive, wrap(dev_tensor(g)), wrap(out))
     ref, ab = oracle.scan_bwd_f32(g, inclusive)
     assert_prefix_close(to_np(out), ref, ab, f"reverse big n={n}")
 
 
-def test_scan_bwd_big_tiles_rows_and_refusal():
+@pytest.mark.parametrize("variant", [5, 6])
+def test_scan_bwd_big_tiles_rows_and_refusal(variant):
     import torch
     from helpers import forced
     sk = skel()
     rows, cols = 3, 40000
     g = syn.uniform_f32(11, rows * cols).reshape(rows, cols)
     out = dev_empty((rows, cols), torch.float32)
-    with forced("scan", 5):
+    with forced("scan", variant):
         sk.skel_scan_bwd("add", True, wrap(dev_tensor(g)), wrap(out))
         o = to_np(out)
         for r in range(rows):

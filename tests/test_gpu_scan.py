@@ -12,9 +12,10 @@ pytestmark = pytest.mark.gpu
 
 SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
 # (variant, ept, tile); variant 5: tile bit 0 publishes the tile aggregate
-# early, bit 1 selects 48 KiB tiles
+# early, bit 1 selects 48 KiB tiles; variant 6: tile 0 = four 48 KiB stages,
+# 1 = six 32 KiB stages
 SCAN_CONFIGS = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (1, 8, 0), (2, 4, 0), (2, 8, 0), (3, 4, 0), (3, 2, 0),
-                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1), (5, 4, 2), (5, 4, 3)]
+                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1), (5, 4, 2), (5, 4, 3), (6, 4, 0), (6, 4, 1)]
 
 
 def mod32(a):
@@ -32,7 +33,7 @@ def test_scan_i32_exact(variant, ept, tile, n, inclusive, pad):
     dx = dev_tensor(x, pad)
     dout = dev_empty((n,), torch.int32, pad)
     with forced("scan", variant, 0, ept, tile):
-        if variant in (4, 5) and pad % 4:
+        if variant in (4, 5, 6) and pad % 4:
             # bulk copies need 16-byte aligned operands; a forced call does not fall back
             with pytest.raises(sk.SkelError) as e:
                 sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
@@ -90,23 +91,26 @@ def test_scan_rows(variant, rows, cols, inclusive):
         assert np.array_equal(gi[r], mod32(oracle.scan_i32(xi[r], inclusive)))
 
 
-def test_scan_lookback_repeated_runs_identical_int():
-    """Races in the look-back would show up as run-to-run differences."""
+@pytest.mark.parametrize("variant,tile", [(1, 0), (6, 0), (6, 1)])
+def test_scan_lookback_repeated_runs_identical_int(variant, tile):
+    """Races in the look-back (or, for the warp-specialised variant, in the
+    hand-over of stages between its roles) would show up as run-to-run
+    differences."""
     import torch
     sk = skel()
-    n = (1 << 22) + 17
+    n = (1 << 22) + 16
     x = syn.uniform_int(7, n, 0, 100)
     dx = wrap(dev_tensor(x))
     ref = mod32(oracle.scan_i32(x, True))
     dout = dev_empty((n,), torch.int32)
-    with forced("scan", 1):
+    with forced("scan", variant, 0, 4 if variant == 6 else 0, tile):
         for _ in range(20):
             dout.fill_(-1)
             sk.skel_scan("add", True, dx, wrap(dout))
             assert np.array_equal(to_np(dout), ref)
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4, 5])
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6])
 def test_scan_types_interleaved_share_lookback_words(variant):
     """int32 and float32 look-back scans alternate on one stream and reuse the
     same descriptor words; a stale word of one type must never read as a
@@ -127,7 +131,7 @@ def test_scan_types_interleaved_share_lookback_words(variant):
         assert_prefix_close(to_np(of), ref, ab, f"interleaved f32 call {k}")
 
 
-@pytest.mark.parametrize("variant", [4, 5])
+@pytest.mark.parametrize("variant", [4, 5, 6])
 @pytest.mark.parametrize("rows,cols", [(3, 5000), (7, 4096), (64, 1000), (2, 12), (3, 40000)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_scan_rows_tma(variant, rows, cols, inclusive):
@@ -143,3 +147,23 @@ def test_scan_rows_tma(variant, rows, cols, inclusive):
     for r in range(rows):
         ref, ab = oracle.scan_f32(x[r], inclusive)
         assert_prefix_close(g[r], ref, ab, f"row {r}")
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_ws_many_ring_turns(tile, inclusive):
+    """2^25 + 4 elements: every persistent block of the warp-specialised
+    variant goes round its ring of stages several times."""
+    import torch
+    sk = skel()
+    n = (1 << 25) + 4
+    xi = syn.uniform_int(900 + tile, n, 0, 100)
+    oi = dev_empty((n,), torch.int32)
+    xf = syn.uniform_f32(901 + tile, n)
+    of = dev_empty((n,), torch.float32)
+    with forced("scan", 6, 0, 4, tile):
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xi)), wrap(oi))
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xf)), wrap(of))
+    assert np.array_equal(to_np(oi), mod32(oracle.scan_i32(xi, inclusive)))
+    ref, ab = oracle.scan_f32(xf, inclusive)
+    assert_prefix_close(to_np(of), ref, ab, f"ws f32 2^25 tile={tile}")
