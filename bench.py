@@ -497,7 +497,8 @@ def config_legs(sk, torch, stream):
     from the step: dot at n = 2^20 (latency-bound, cold and warm L2), a
     10-call 9-point stencil chain on 8192^2 (composed vs one call per step),
     the batched instances as one CUDA-graph replay against 2 x 4096 separate
-    calls, and forward + backward of the composed loss on 8192^2."""
+    calls, forward + backward of the composed loss on 8192^2, and the host
+    edge variants on host-resident inputs."""
     dev = torch.device("cuda")
     out = {}
     # dot, n = 2^20
@@ -589,7 +590,43 @@ def config_legs(sk, torch, stream):
     fwd_bwd()
     ms_ad = _event_ms(torch, stream, fwd_bwd, 5)
     out["autograd_8192sq"] = {"ms_fwd_bwd": round(ms_ad, 3)}
+    out["host_edge_2e26"] = host_edge_leg(sk, torch, stream)
     return out
+
+
+def host_edge_leg(sk, torch, stream):
+    """Map (axpy), Reduce (sum) and MapReduce (dot) on 2^26-element inputs
+    valid only in pinned host memory at every call, through each host-edge
+    variant (whole copy, chunked copy pipeline, direct reads of host memory):
+    ms per call and GB/s of the bytes that cross the host link."""
+    n = 1 << 26
+    dev = torch.device("cuda")
+    hx = torch.from_numpy(syn.uniform_f32(syn.SEED_X, n)).pin_memory()
+    hy = torch.from_numpy(syn.uniform_f32(syn.SEED_Y, n)).pin_memory()
+    cx, cy = sk.Container.from_host(hx.numpy()), sk.Container.from_host(hy.numpy())
+    o, r = torch.empty(n, device=dev), torch.zeros(1, device=dev)
+    co, cr = sk.Container.from_tensor(o), sk.Container.from_tensor(r)
+    calls = {"map_axpy": (lambda: sk.skel_map("axpy", [cx, cy], co, [2.5]), 8 * n),
+             "reduce_sum": (lambda: sk.skel_reduce("add", cx, cr, host=False), 4 * n),
+             "mapreduce_dot": (lambda: sk.skel_mapreduce("mul", "add", [cx, cy], cr, host=False), 8 * n)}
+    res = {}
+    for vname, (v, tile) in {"copy": (0, 0), "chunked_8MiB": (1, 0), "chunked_32MiB": (1, 1),
+                             "direct": (2, 0)}.items():
+        sk.skel_force_variant("edge", v, 0, 0, tile)
+        try:
+            for cname, (fn, link_bytes) in calls.items():
+                def one():
+                    cx.mark(sk.UNIT_HOST)
+                    cy.mark(sk.UNIT_HOST)
+                    fn()
+                one()
+                ms = _event_ms(torch, stream, one, 5)
+                res.setdefault(cname, {})[vname] = {"ms": round(ms, 3), "link_GB/s": round(link_bytes / ms / 1e6, 1)}
+        finally:
+            sk.skel_force_variant("edge", -1)
+    for c in (cx, cy, co, cr):
+        c.close()
+    return res
 
 
 # -------------------------------------------------------------------- main --

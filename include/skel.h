@@ -118,7 +118,8 @@ typedef enum {
     SKEL_SK_MAPARRAY = 6,
     SKEL_SK_BATCHED = 7,
     SKEL_SK_CHAIN2D = 8,   /* a chain of 2D MapOverlap calls (skel_mapoverlap_chain) */
-    SKEL_SK_COUNT = 9
+    SKEL_SK_EDGE = 9,      /* host edge of Map / Reduce / MapReduce calls on host-only inputs */
+    SKEL_SK_COUNT = 10
 } skel_skeleton;
 
 /* ------------------------------------------------------------ library --- */
@@ -417,6 +418,32 @@ int skel_force_variant(int skeleton, int variant, int block, int ept, int tile);
 /* Variant, block, ept and tile the last call of `skeleton` ran with on this
  * thread (all -1 before the first call). */
 int skel_last_variant(int skeleton, int *variant, int *block, int *ept, int *tile);
+
+/* The host edge (SKEL_SK_EDGE; Sec. IV lazy copying, keyed by residency).
+ * A Map, Reduce or MapReduce call with an input whose valid copy is only in
+ * host memory first chooses, from the entries of skeleton SKEL_SK_EDGE
+ * (fn = the calling skeleton: SKEL_SK_MAP, SKEL_SK_REDUCE or
+ * SKEL_SK_MAPREDUCE; residency 1), how those bytes cross the host link:
+ *   variant 0 copy:    the whole lazy copy, then the call (the default);
+ *   variant 1 chunked: the copy in chunks of 8 MiB << (2 * tile) bytes
+ *                      (tile 0..3) on a library-owned copy stream, each
+ *                      chunk's part of the call started on `stream` as soon
+ *                      as the chunk has landed; afterwards the input is valid
+ *                      on both units, as after the whole copy.  Needs inputs
+ *                      that cover their whole storage (no views);
+ *   variant 2 direct:  the kernels read the host copy in place over the link;
+ *                      no device copy is made and the input stays valid only
+ *                      on the host.  Needs pinned host memory (cudaMallocHost,
+ *                      cudaHostAlloc or registered); the caller must not
+ *                      write the host copy until `stream` has finished the
+ *                      call, as for an asynchronous copy.
+ * Neither 1 nor 2 applies when the output shares storage with a host-only
+ * input.  Second touch: an input that has already been read in place (2)
+ * since its host copy was last written (host write access, or
+ * skel_container_mark) is being reused, so a table choice of 2 becomes 0 for
+ * it and later calls find it on the device.  A variant that does not apply falls back to 0 (or, when forced,
+ * makes the call return SKEL_ERR_UNSUPPORTED).  skel_last_variant(SKEL_SK_EDGE)
+ * reports the choice of the last such call. */
 
 /* Number of variants of a skeleton and the name of variant v (static). */
 int skel_variant_count(int skeleton);

@@ -22,7 +22,7 @@ BOUNDARY = {"clamp": 0, "zero": 1, "periodic": 2}
 READ, WRITE, READWRITE = 1, 2, 3
 UNIT_HOST, UNIT_DEVICE = 1, 2
 SK = {"map": 0, "reduce": 1, "mapreduce": 2, "scan": 3, "mapoverlap1d": 4, "mapoverlap2d": 5,
-      "maparray": 6, "batched": 7, "chain2d": 8}
+      "maparray": 6, "batched": 7, "chain2d": 8, "edge": 9}
 
 vp, i32, i64, dbl, f32p = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_float)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)

@@ -40,6 +40,7 @@ struct Storage {
     int valid = 0;                    // bits of skel_unit holding a valid copy
     cudaStream_t last_stream = nullptr;
     bool used_on_device = false;      // some device work on the storage was enqueued
+    int direct_reads = 0;             // device reads of the host copy in place since it was last written
     int64_t h2d_count = 0, d2h_count = 0, h2d_bytes = 0, d2h_bytes = 0;
 };
 
@@ -147,6 +148,7 @@ int acquire_host(skel_handle h, int mode, cudaStream_t s, void **ptr)
     if (st->used_on_device) SKEL_CUDA_TRY(cudaStreamSynchronize(st->last_stream));
     int nv, tr;
     coherence_step(st->valid, SKEL_UNIT_HOST, mode, &nv, &tr);
+    if (mode & SKEL_WRITE) st->direct_reads = 0;
     if (tr == 2) {
         SKEL_CUDA_TRY(cudaMemcpyAsync(st->host, st->dev, st->bytes, cudaMemcpyDeviceToHost, s));
         SKEL_CUDA_TRY(cudaStreamSynchronize(s));
@@ -302,6 +304,7 @@ int skel_container_mark(skel_handle h, int units)
         if ((units & SKEL_UNIT_HOST) && !h->st->host) return fail(SKEL_ERR_INVALID_ARG, "no host copy exists");
         if ((units & SKEL_UNIT_DEVICE) && !h->st->dev) return fail(SKEL_ERR_INVALID_ARG, "no device copy exists");
         h->st->valid = units;
+        h->st->direct_reads = 0;
         return (int)SKEL_OK;
     });
 }
@@ -472,6 +475,246 @@ Choice st2_def() { return stencil_default(2); }
 Choice ma_def() { return maparray_default(); }
 Choice bat_def() { return batched_default(); }
 
+// ------------------------------------------------------------ host edge --
+// A call whose inputs are valid only in host memory (residency 1) first
+// chooses how those bytes cross the host link (Sec. IV: the lazy copy is the
+// container protocol; where it happens is an implementation choice, tuned
+// per residency like any other variant):
+//   0 copy     the whole lazy copy, then the call (the protocol as it stands);
+//   1 chunked  the copy split into chunks on a copy stream; each chunk's part
+//              of the call starts as soon as its chunk has landed, so link
+//              and kernels overlap; the device copy ends valid, as with 0
+//              (containers covering their whole storage only);
+//   2 direct   the kernels read the pinned host copy in place over the link;
+//              no device copy is made and the container stays valid only on
+//              the host (pinned host memory only).
+// Offered for Map, Reduce and MapReduce (the streaming skeletons); tile
+// selects the chunk: 8 MiB << (2 * tile).
+enum { kEdgeCopy = 0, kEdgeChunked = 1, kEdgeDirect = 2 };
+
+bool host_only(skel_handle h) { return (h->st->valid & SKEL_UNIT_HOST) && !(h->st->valid & SKEL_UNIT_DEVICE); }
+
+bool whole_storage(skel_handle h) { return h->offset == 0 && (size_t)h->n * dtype_size(h->dtype) == h->st->bytes; }
+
+// The device's address of a host-only operand's pinned host copy; nullptr
+// when the host copy is pageable.
+const void *pinned_view(skel_handle h)
+{
+    cudaPointerAttributes a{};
+    if (!h->st->host || cudaPointerGetAttributes(&a, h->st->host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return static_cast<const char *>(a.devicePointer) + h->offset;
+}
+
+std::mutex g_copy_mu;
+cudaStream_t g_copy_stream[64] = {};
+
+int copy_stream(cudaStream_t *out)
+{
+    int dev = 0;
+    SKEL_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(SKEL_ERR_UNSUPPORTED, "host edge: device index out of range");
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    if (!g_copy_stream[dev]) SKEL_CUDA_TRY(cudaStreamCreateWithFlags(&g_copy_stream[dev], cudaStreamNonBlocking));
+    *out = g_copy_stream[dev];
+    return SKEL_OK;
+}
+
+// One input of an edge call: its device-side address, and whether its bytes
+// still have to cross the link (host-only, first occurrence of its storage).
+struct EdgeIn {
+    skel_handle h;
+    bool host = false;
+    bool first = true;
+    const void *ptr = nullptr;
+};
+
+// The residency class of a call's READ operands, without acquiring them.
+int residency_of(const std::vector<skel_handle> &ins)
+{
+    for (skel_handle h : ins)
+        if (host_only(h)) return 1;
+    return 0;
+}
+
+// Checks that edge variant v applies (before any state changes), then
+// acquires the inputs: device-valid ones as usual, host-only ones with a
+// device allocation and no copy (chunked) or at their pinned host address
+// (direct).  The output must not share storage with a host-only input.
+int edge_prepare(std::vector<EdgeIn> &ins, skel_handle out, int v, cudaStream_t s)
+{
+    for (size_t i = 0; i < ins.size(); ++i) {
+        EdgeIn &e = ins[i];
+        e.host = host_only(e.h);
+        for (size_t j = 0; j < i; ++j)
+            if (ins[j].h->st == e.h->st) e.first = false;
+        if (!e.host) continue;
+        if (out && same_storage(out, e.h)) return fail(SKEL_ERR_UNSUPPORTED, "host edge: output aliases a host-only input");
+        if (v == kEdgeChunked && !whole_storage(e.h))
+            return fail(SKEL_ERR_UNSUPPORTED, "chunked host edge: views are copied whole");
+        if (v == kEdgeDirect && e.h->n > 0 && !pinned_view(e.h))
+            return fail(SKEL_ERR_UNSUPPORTED, "direct host edge: the host copy is not pinned");
+    }
+    for (EdgeIn &e : ins) {
+        Storage *st = e.h->st;
+        if (!e.host) {
+            void *p = nullptr;
+            int rc = acquire_device(e.h, SKEL_READ, s, &p);
+            if (rc) return rc;
+            e.ptr = p;
+            continue;
+        }
+        int rc = order_after_last_use(st, s);
+        if (rc) return rc;
+        if (v == kEdgeDirect) {
+            e.ptr = e.h->n > 0 ? pinned_view(e.h) : nullptr;   // nothing to read when empty
+            if (e.first) st->direct_reads += 1;
+        } else {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            if (st->dev && st->device >= 0 && st->device != dev)
+                return fail(SKEL_ERR_INVALID_ARG, "container device memory belongs to another device");
+            if (!st->dev) {
+                st->dev_alloc_rec = current_allocator();
+                st->dev = dev_alloc(st->dev_alloc_rec, st->bytes, s);
+                if (!st->dev) return fail(SKEL_ERR_OOM, "device allocation of container failed");
+                st->dev_owned = true;
+                st->device = dev;
+            }
+            e.ptr = static_cast<char *>(st->dev) + e.h->offset;
+        }
+        st->last_stream = s;
+        st->used_on_device = true;
+    }
+    return SKEL_OK;
+}
+
+// The chunked pipeline: chunk k of every host-only input goes over the link
+// on the copy stream, then `launch(off, len, k)` runs that chunk's part of
+// the call on s.  The copy stream first waits for the work already queued
+// on s (earlier users of the device copies).  Afterwards the host-only
+// inputs are valid on both units, as after the whole lazy copy.
+template <class Launch>
+int edge_chunked(std::vector<EdgeIn> &ins, int64_t n, size_t es, int tile, cudaStream_t s, Launch launch)
+{
+    if (tile < 0 || tile > 3) return fail(SKEL_ERR_INVALID_ARG, "host edge: tile (chunk size) must be 0..3");
+    const int64_t chunk = (int64_t)((size_t(8) << 20 << (2 * tile)) / es);
+    cudaStream_t cs;
+    int rc = copy_stream(&cs);
+    if (rc) return rc;
+    cudaEvent_t ev;
+    SKEL_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    auto hop = [&](cudaStream_t from, cudaStream_t to) -> cudaError_t {   // `to` waits for `from`
+        cudaError_t e = cudaEventRecord(ev, from);
+        return e == cudaSuccess ? cudaStreamWaitEvent(to, ev, 0) : e;
+    };
+    cudaError_t e = hop(s, cs);
+    for (int64_t off = 0, k = 0; e == cudaSuccess && off < n; off += chunk, ++k) {
+        const int64_t len = n - off < chunk ? n - off : chunk;
+        for (const EdgeIn &in : ins) {
+            if (!in.host || !in.first || e != cudaSuccess) continue;
+            e = cudaMemcpyAsync(const_cast<char *>(static_cast<const char *>(in.ptr)) + off * es,
+                                static_cast<const char *>(in.h->st->host) + in.h->offset + off * es, (size_t)len * es,
+                                cudaMemcpyHostToDevice, cs);
+        }
+        if (e == cudaSuccess) e = hop(cs, s);
+        if (e == cudaSuccess && (rc = launch(off, len, k))) break;
+    }
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return fail_cuda(e, "chunked host edge");
+    if (rc) return rc;
+    for (const EdgeIn &in : ins) {
+        if (!in.host || !in.first) continue;
+        Storage *st = in.h->st;
+        st->valid |= SKEL_UNIT_DEVICE;
+        st->h2d_count += 1;
+        st->h2d_bytes += (int64_t)st->bytes;
+    }
+    return SKEL_OK;
+}
+
+// The table's choice for a call on host-only inputs.  Second touch: an
+// input already read in place since its host copy was last written is being
+// reused, so a direct choice becomes the whole copy (later calls then find
+// it on the device) unless the variant is forced.
+Choice edge_choice(int sk, int dt, int64_t n, const skel_handle *ins, int nin, bool *forced)
+{
+    Choice c = select_variant(Context{SKEL_SK_EDGE, sk, dt, n, 0, 1}, forced);
+    if (c.variant == kEdgeDirect && !*forced)
+        for (int k = 0; k < nin; ++k)
+            if (host_only(ins[k]) && ins[k]->st->direct_reads > 0) return Choice{kEdgeCopy, 0, 0, 0};
+    return c;
+}
+
+// Map through edge variant 1 or 2; SKEL_ERR_UNSUPPORTED (nothing done) when
+// the variant does not apply to this call.
+int map_edge(int fn, float a, const skel_handle *ins, int nin, skel_handle out, const Choice &ec, cudaStream_t s)
+{
+    std::vector<EdgeIn> ei;
+    for (int k = 0; k < nin; ++k) ei.push_back(EdgeIn{ins[k]});
+    int rc = edge_prepare(ei, out, ec.variant, s);
+    if (rc) return rc;
+    void *po = nullptr;
+    if ((rc = acquire_device(out, SKEL_WRITE, s, &po))) return rc;
+    const float *i0 = (const float *)ei[0].ptr, *i1 = nin == 2 ? (const float *)ei[1].ptr : nullptr;
+    float *o = (float *)po;
+    auto run = [&](int64_t off, int64_t len, int res) {
+        MapLaunch m{fn, a, i0 + off, i1 ? i1 + off : nullptr, o + off, len};
+        Context ctx{SKEL_SK_MAP, fn, SKEL_F32, len, 0, res};
+        return run_with_fallback(SKEL_SK_MAP, ctx, [&](const Choice &c) { return launch_map(m, c, s); }, map_def);
+    };
+    if (ec.variant == kEdgeDirect) return run(0, out->n, 1);
+    return edge_chunked(ei, out->n, 4, ec.tile, s, [&](int64_t off, int64_t len, int64_t) { return run(off, len, 0); });
+}
+
+// Reduce / MapReduce through edge variant 1 or 2.  Chunked: each chunk's
+// reduction writes its own partial; one more reduction (op, or + for
+// MapReduce) adds the partials up into `out`.
+int reduce_edge(int sk, int map_fn, int op, const skel_handle *ins, int nin, skel_handle result_dev, void **outp,
+                const Choice &ec, cudaStream_t s)
+{
+    std::vector<EdgeIn> ei;
+    for (int k = 0; k < nin; ++k) ei.push_back(EdgeIn{ins[k]});
+    int rc = edge_prepare(ei, result_dev, ec.variant, s);
+    if (rc) return rc;
+    void *out = nullptr;
+    if (result_dev) rc = acquire_device(result_dev, SKEL_WRITE, s, &out);
+    else rc = result_slot(s, &out);
+    if (rc) return rc;
+    *outp = out;
+    const int dt = ins[0]->dtype;
+    const int64_t n = ins[0]->n;
+    const size_t es = dtype_size(dt);
+    const int fkey = sk == SKEL_SK_MAPREDUCE ? map_fn : op;
+    auto run = [&](int64_t off, int64_t len, void *dst, int res) {
+        ReduceLaunch r{op, map_fn, dt, static_cast<const char *>(ei[0].ptr) + off * es,
+                       nin == 2 ? static_cast<const char *>(ei[1].ptr) + off * es : nullptr, dst, len};
+        Context ctx{sk, fkey, dt, len, 0, res};
+        return run_with_fallback(sk, ctx, [&](const Choice &c) { return launch_reduce(r, c, s); }, reduce_def);
+    };
+    if (ec.variant == kEdgeDirect) return run(0, n, out, 1);
+    if (ec.tile < 0 || ec.tile > 3) return fail(SKEL_ERR_INVALID_ARG, "host edge: tile (chunk size) must be 0..3");
+    const int64_t chunk = (int64_t)((size_t(8) << 20 << (2 * ec.tile)) / es);
+    const int64_t nchunks = n == 0 ? 1 : (n + chunk - 1) / chunk;
+    const Allocator rec = current_allocator();
+    char *partials = static_cast<char *>(dev_alloc(rec, (size_t)nchunks * es, s));
+    if (!partials) return fail(SKEL_ERR_OOM, "host edge: partial results");
+    rc = edge_chunked(ei, n, es, ec.tile, s,
+                      [&](int64_t off, int64_t len, int64_t k) { return run(off, len, partials + k * es, 0); });
+    if (!rc && n == 0) rc = run(0, 0, partials, 0);   // the identity
+    if (!rc) {
+        ReduceLaunch r{sk == SKEL_SK_MAPREDUCE ? (int)SKEL_FN_ADD : op, -1, dt, partials, nullptr, out, nchunks};
+        Context ctx{SKEL_SK_REDUCE, r.op, dt, nchunks, 0, 0};
+        rc = run_with_fallback(SKEL_SK_REDUCE, ctx, [&](const Choice &c) { return launch_reduce(r, c, s); }, reduce_def);
+    }
+    dev_free(rec, partials, s);
+    return rc;
+}
+
+
 int reduce_common(int sk, int map_fn, int op, const skel_handle *ins, int nin, void *result_host,
                   skel_handle result_dev, cudaStream_t s)
 {
@@ -483,6 +726,23 @@ int reduce_common(int sk, int map_fn, int op, const skel_handle *ins, int nin, v
     if (!result_host && !result_dev) return fail(SKEL_ERR_INVALID_ARG, "no result destination");
     if (result_dev && (!valid_handle(result_dev) || result_dev->n != 1 || result_dev->dtype != dt))
         return fail(SKEL_ERR_SHAPE, "result container must hold 1 element of the input dtype");
+    if (residency_of(std::vector<skel_handle>(ins, ins + nin))) {
+        bool forced = false;
+        const Choice ec = edge_choice(sk, dt, ins[0]->n, ins, nin, &forced);
+        if (ec.variant == kEdgeChunked || ec.variant == kEdgeDirect) {
+            void *out = nullptr;
+            int rc = reduce_edge(sk, map_fn, op, ins, nin, result_dev, &out, ec, s);
+            if (rc == SKEL_OK) {
+                record_last(SKEL_SK_EDGE, ec);
+                return result_host ? copy_result_to_host(result_host, out, 4, s) : (int)SKEL_OK;
+            }
+            if (rc != SKEL_ERR_UNSUPPORTED || forced) return rc;
+            clear_error();   // not applicable: the whole lazy copy
+        } else if (ec.variant != kEdgeCopy) {
+            return fail(SKEL_ERR_INVALID_ARG, "host edge: unknown variant");
+        }
+        record_last(SKEL_SK_EDGE, Choice{kEdgeCopy, 0, 0, 0});
+    }
     std::vector<Operand> ops;
     for (int k = 0; k < nin; ++k) ops.push_back({ins[k], SKEL_READ});
     if (result_dev) ops.push_back({result_dev, SKEL_WRITE});
@@ -586,13 +846,30 @@ int skel_map(skel_fn fn, const double *params, int nparams, const skel_handle *i
         }
         if (out->dtype != SKEL_F32) return fail(SKEL_ERR_DTYPE, "map: float32 only");
         cudaStream_t s = (cudaStream_t)stream;
+        const float a = map_needs_param(fn) ? (float)params[0] : 0.f;
+        if (residency_of(std::vector<skel_handle>(ins, ins + nin))) {
+            bool forced = false;
+            const Choice ec = edge_choice(SKEL_SK_MAP, SKEL_F32, out->n, ins, nin, &forced);
+            if (ec.variant == kEdgeChunked || ec.variant == kEdgeDirect) {
+                int rc = map_edge(fn, a, ins, nin, out, ec, s);
+                if (rc == SKEL_OK) {
+                    record_last(SKEL_SK_EDGE, ec);
+                    return rc;
+                }
+                if (rc != SKEL_ERR_UNSUPPORTED || forced) return rc;
+                clear_error();   // not applicable: the whole lazy copy
+            } else if (ec.variant != kEdgeCopy) {
+                return fail(SKEL_ERR_INVALID_ARG, "host edge: unknown variant");
+            }
+            record_last(SKEL_SK_EDGE, Choice{kEdgeCopy, 0, 0, 0});
+        }
         std::vector<Operand> ops;
         for (int k = 0; k < nin; ++k) ops.push_back({ins[k], SKEL_READ});
         ops.push_back({out, SKEL_WRITE});
         int res = 0;
         int rc = acquire_all(ops, s, &res);
         if (rc) return rc;
-        MapLaunch m{fn, map_needs_param(fn) ? (float)params[0] : 0.f, (const float *)ops[0].ptr,
+        MapLaunch m{fn, a, (const float *)ops[0].ptr,
                     nin == 2 ? (const float *)ops[1].ptr : nullptr, (float *)ops.back().ptr, out->n};
         Context ctx{SKEL_SK_MAP, fn, SKEL_F32, out->n, 0, res};
         return run_with_fallback(SKEL_SK_MAP, ctx, [&](const Choice &c) { return launch_map(m, c, s); }, map_def);
@@ -1129,6 +1406,7 @@ int skel_variant_count(int skeleton)
     case SKEL_SK_MAPARRAY: return maparray_variant_count();
     case SKEL_SK_BATCHED: return batched_variant_count();
     case SKEL_SK_CHAIN2D: return chain_variant_count();
+    case SKEL_SK_EDGE: return 3;
     default: return 0;
     }
 }
@@ -1144,6 +1422,10 @@ const char *skel_variant_name(int skeleton, int variant)
     case SKEL_SK_MAPARRAY: return maparray_variant_name(variant);
     case SKEL_SK_BATCHED: return batched_variant_name(variant);
     case SKEL_SK_CHAIN2D: return chain_variant_name(variant);
+    case SKEL_SK_EDGE: {
+        static const char *names[] = {"copy", "chunked", "direct"};
+        return variant >= 0 && variant < 3 ? names[variant] : "?";
+    }
     default: return "?";
     }
 }

@@ -28,7 +28,7 @@ import time
 import numpy as np
 import torch
 
-from . import (F32, I32, SK, Container, SkelError, skel_batched, skel_force_variant, skel_load_dispatch_table,
+from . import (F32, I32, SK, UNIT_HOST, Container, SkelError, skel_batched, skel_force_variant, skel_load_dispatch_table,
                skel_map, skel_mapoverlap, skel_mapoverlap_chain, skel_maparray, skel_maparray_grid, skel_mapreduce,
                skel_reduce, skel_scan, skel_scan_bwd)
 from ._lib import FN
@@ -105,6 +105,11 @@ def candidates(sk_name: str):
         yield (0, 0, 0, 0)
         for k in (1, 2, 3, 4, 5, 6, 8):
             yield (1, 256, 0, k)
+    elif sk_name == "edge":
+        yield (0, 0, 0, 0)
+        for t in (0, 1, 2):      # chunks of 8, 32, 128 MiB
+            yield (1, 0, 0, t)
+        yield (2, 0, 0, 0)
     elif sk_name == "batched":
         for v in (0, 1, 2, 4):
             for e in (2, 4, 8):
@@ -118,9 +123,10 @@ class Instance:
     """One skeleton instance (skeleton + user function + dtype) with buffers
     for its largest size; call(n) runs it on the first n elements."""
 
-    def __init__(self, name, sk_name, fn_key, dtype, radius, nmax, make, nbytes, sizes):
+    def __init__(self, name, sk_name, fn_key, dtype, radius, nmax, make, nbytes, sizes, residency=0):
         self.name, self.sk_name, self.fn_key, self.dtype, self.radius = name, sk_name, fn_key, dtype, radius
         self.nmax, self.make, self.nbytes, self.sizes = nmax, make, nbytes, sizes
+        self.residency = residency
 
 
 def instances(nmax_log2: int):
@@ -304,6 +310,43 @@ def instances(nmax_log2: int):
     csizes = [q for q in sizes if q <= (1 << 20)]
     out.append(Instance("maparray coulomb f32 (1024 atoms)", "maparray", FN["coulomb"], F32, 0, 1 << 21, mk_coulomb(),
                         lambda n: 4 * n, csizes))
+
+    # the host edge: inputs valid only in pinned host memory at every call
+    # (residency 1); the bytes counted are the call's own, so the rates are
+    # bounded by the host link, not by HBM
+    emax = min(nmax, 1 << 26)
+    esizes = [s for s in sizes if (1 << 16) <= s <= emax]
+
+    def mk_edge(kind):
+        bufs = {}
+
+        def make(n):
+            if "x" not in bufs:
+                bufs["x"] = torch.rand(emax).pin_memory()
+                bufs["y"] = torch.rand(emax).pin_memory()
+                bufs["o"], bufs["r"] = vec(emax), torch.zeros(1, device=dev)
+            cx = Container.from_host(bufs["x"].numpy()[:n])
+            cy = Container.from_host(bufs["y"].numpy()[:n])
+            co, cr = Container.from_tensor(bufs["o"][:n]), Container.from_tensor(bufs["r"])
+
+            def call():
+                cx.mark(UNIT_HOST)
+                cy.mark(UNIT_HOST)
+                if kind == "map":
+                    skel_map("axpy", [cx, cy], co, [2.5])
+                elif kind == "reduce":
+                    skel_reduce("add", cx, cr, host=False)
+                else:
+                    skel_mapreduce("mul", "add", [cx, cy], cr, host=False)
+            return call
+        return make
+
+    out.append(Instance("host edge: map axpy f32", "edge", SK["map"], F32, 0, emax, mk_edge("map"),
+                        lambda n: 12 * n, esizes, residency=1))
+    out.append(Instance("host edge: reduce add f32", "edge", SK["reduce"], F32, 0, emax, mk_edge("reduce"),
+                        lambda n: 4 * n, esizes, residency=1))
+    out.append(Instance("host edge: mapreduce dot f32", "edge", SK["mapreduce"], F32, 0, emax, mk_edge("mapreduce"),
+                        lambda n: 8 * n, esizes, residency=1))
     return out
 
 
@@ -429,13 +472,13 @@ def tune(args):
             last = r
             best, t_def, t_tuned, nb = r
             if best is not None:
-                lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 "
+                lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} {inst.residency} "
                              f"{best[0]} {best[1]} {best[2]} {best[3]}")
                 chosen = best
             else:
                 # record that the default won here, so this bucket never
                 # inherits a neighbouring bucket's choice by extrapolation
-                lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} 0 -1 0 0 0")
+                lines.append(f"{sk_id} {inst.fn_key} {inst.dtype} {bucket(n)} {inst.radius} {inst.residency} -1 0 0 0")
                 chosen = "default"
             chosen_all.append((inst.name, n, chosen))
             if sampled:
