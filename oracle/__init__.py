@@ -71,6 +71,7 @@ def _load():
                 "oracle_composed_loss_f32": (d, [vp, i64, i64, i32, vp, i32, vp]),
                 "oracle_composed_loss_f64": (d, [vp, i64, i64, i32, vp, i32]),
                 "oracle_composed_loss_delta_f32": (d, [vp, i64, i64, i32, vp, i32, i64, i64, d]),
+                "oracle_chain_map_stencil_sumsq_f32": (d, [i32, d, vp, i64, i64, i32, vp, i32, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -269,6 +270,17 @@ def composed_loss_f32(x, r: int, w, boundary: str = "clamp", grad: bool = True):
     L = _load().oracle_composed_loss_f32(_p(x), x.shape[0], x.shape[1], r, _p(w),
                                          BOUNDARY[boundary], _p(g))
     return L, g
+
+
+def chain_map_stencil_sumsq_f32(fn: str, x, r: int, w, boundary: str = "clamp", a: float = 0.0):
+    """Returns (sum_p (S f(x))_p^2, sum_p (sum_taps |w| |f(x)|)^2): the chain
+    Map -> 2D MapOverlap -> MapReduce(sq, +) on a 2D float32 grid, and the
+    scale of its float32 rounding bound."""
+    x, w = _f32(x), _f32(w)
+    bound = C.c_double(0.0)
+    v = _load().oracle_chain_map_stencil_sumsq_f32(FN[fn], float(a), _p(x), x.shape[0], x.shape[1], r, _p(w),
+                                                   BOUNDARY[boundary], C.byref(bound))
+    return v, bound.value
 
 
 def composed_loss_f64(x, r: int, w, boundary: str = "clamp") -> float:

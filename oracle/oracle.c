@@ -19,6 +19,10 @@
  *     out[i] = f(A, B[i]) with A read whole (random access) and B per element
  *     (or, for the Coulombic potential grid of Sec. III, the element's own
  *     grid position).
+ *   - Sec. II (composition of components): a chain of calls is the
+ *     definitions applied one after the other, every intermediate kept in
+ *     float64 (oracle_mapoverlap2d_chain_f32, the composed loss and
+ *     oracle_chain_map_stencil_sumsq_f32).
  *   - Backward passes are the adjoints of these linear/elementwise maps,
  *     written from their definitions (scatter form), not from the GPU design.
  *
@@ -488,6 +492,45 @@ double oracle_composed_loss_f64(const double *x, int64_t rows, int64_t cols, int
     for (int64_t p = 0; p < N; ++p) C += s[p] * s[p];
     free(t); free(u); free(s);
     return L1 + C / (double)N;
+}
+
+/* The chain Map -> MapOverlap -> MapReduce as three composed skeleton calls
+ * (Sec. II: a composition of components; here the definitions applied one
+ * after the other, every intermediate in float64):
+ *   t = f(x)                   Sec. III map with a unary user function
+ *   u = S t                    2D mapoverlap, the definition of
+ *                              oracle_mapoverlap2d_f32 applied to t
+ *   result = sum_p u_p^2       MapReduce with sq and +
+ * *bound receives sum_p (sum_taps |w| |t|)^2, the scale of the rounding error
+ * of a float32 evaluation of the chain (every tap of every stencil output at
+ * its largest magnitude, squared).  Returns the result. */
+double oracle_chain_map_stencil_sumsq_f32(int fn, double a, const float *x, int64_t rows, int64_t cols, int r,
+                                          const float *w, int boundary, double *bound)
+{
+    const int64_t N = rows * cols;
+    const int side = 2 * r + 1;
+    double *t = malloc(sizeof(double) * (N > 0 ? N : 1)), *u = malloc(sizeof(double) * (N > 0 ? N : 1));
+    if (!t || !u) { free(t); free(u); return NAN; }
+    for (int64_t p = 0; p < N; ++p) t[p] = map_fn(fn, a, (double)x[p], 0.0);
+    stencil2d_f64(t, rows, cols, r, w, boundary, u);
+    double sum = 0.0, scale = 0.0;
+    for (int64_t p = 0; p < N; ++p) sum += u[p] * u[p];
+    for (int64_t i = 0; i < rows; ++i)
+        for (int64_t j = 0; j < cols; ++j) {
+            double m = 0.0;
+            for (int di = -r; di <= r; ++di) {
+                int64_t si = bmap(i + di, rows, boundary);
+                for (int dj = -r; dj <= r; ++dj) {
+                    int64_t sj = bmap(j + dj, cols, boundary);
+                    if (si < 0 || sj < 0) continue;
+                    m += fabs((double)w[(di + r) * side + (dj + r)]) * fabs(t[si * cols + sj]);
+                }
+            }
+            scale += m * m;
+        }
+    if (bound) *bound = scale;
+    free(t); free(u);
+    return sum;
 }
 
 /* Local change of the composed loss when x[pi,pj] moves from x0 to x0 + h,

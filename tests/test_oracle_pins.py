@@ -437,6 +437,70 @@ def test_composed_loss_local_delta_equals_full_difference(boundary):
         assert abs(full - local) <= 1e-12 * max(1.0, abs(base))
 
 
+# ------------------------------------- Map -> MapOverlap -> MapReduce chain ---
+UNARY = {"copy": lambda t, a: t, "sq": lambda t, a: t * t, "scale": lambda t, a: a * t, "tanh": lambda t, a: np.tanh(t)}
+
+
+@pytest.mark.parametrize("fn,a", [("copy", 0.0), ("sq", 0.0), ("scale", 2.5), ("tanh", 0.0)])
+@pytest.mark.parametrize("boundary", ["clamp", "periodic"])
+def test_chain_constant_grid_closed_form(fn, a, boundary):
+    """A constant grid c: every stencil output is f(c) (weights sum to 1,
+    CLAMP and PERIODIC read only c), so the chain is rows * cols * f(c)^2."""
+    c = 0.625
+    x = np.full((9, 13), c, np.float32)
+    for kind in ("5pt", "9pt"):
+        v, bound = oracle.chain_map_stencil_sumsq_f32(fn, x, 1, oracle.stencil_weights(kind), boundary, a)
+        fc = UNARY[fn](c, a) if fn != "tanh" else math.tanh(c)
+        assert v == pytest.approx(9 * 13 * fc * fc, rel=1e-14)
+        assert bound == pytest.approx(v, rel=1e-14)   # nonnegative weights and values: no cancellation
+
+
+@pytest.mark.parametrize("boundary,scale", [("clamp", 1.0), ("periodic", 1.0), ("zero", 0.25)])
+def test_chain_one_cell_grid(boundary, scale):
+    """1 x 1 grid, 9-point weights: CLAMP and PERIODIC read the cell at every
+    tap (sum of weights 1), ZERO only at the centre (weight 1/4)."""
+    x = np.array([[0.75]], np.float32)
+    v, _ = oracle.chain_map_stencil_sumsq_f32("scale", x, 1, oracle.stencil_weights("9pt"), boundary, 2.0)
+    assert v == (scale * 1.5) ** 2
+
+
+@pytest.mark.parametrize("fn,a", [("copy", 0.0), ("sq", 0.0), ("scale", -1.5), ("tanh", 0.0)])
+@pytest.mark.parametrize("boundary", ["clamp", "zero", "periodic"])
+@pytest.mark.parametrize("shape", [(1, 1), (2, 3), (5, 4), (6, 6)])
+def test_chain_is_dense_matrix_form(fn, a, boundary, shape):
+    """r = |S f(x)|^2 with S the dense stencil matrix (built by scipy's
+    correlate) and f applied by numpy."""
+    w = syn.uniform_f32(60, 9, -1.0, 1.0).reshape(3, 3)
+    x = syn.uniform_f32(61, shape[0] * shape[1]).reshape(shape)
+    S = dense_stencil_matrix_2d(shape[0], shape[1], 1, w, boundary)
+    u = S @ UNARY[fn](x.astype(np.float64).ravel(), a)
+    v, bound = oracle.chain_map_stencil_sumsq_f32(fn, x, 1, w, boundary, a)
+    assert v == pytest.approx(float(u @ u), rel=1e-12, abs=1e-300)
+    # sum over the taps of |w| |t| per output: the stencil matrix of |w|
+    # (taps that read the same cell add up, each with its own |w|)
+    Sa = dense_stencil_matrix_2d(shape[0], shape[1], 1, np.abs(w), boundary)
+    m = Sa @ np.abs(UNARY[fn](x.astype(np.float64).ravel(), a))
+    assert bound == pytest.approx(float(m @ m), rel=1e-12, abs=1e-300)
+    assert bound >= v - 1e-12 * abs(v)
+
+
+def test_chain_copy_is_mapoverlap_then_sumsq():
+    x = syn.uniform_f32(62, 33 * 47).reshape(33, 47)
+    for kind, boundary in (("9pt", "clamp"), ("5pt", "zero"), ("9pt", "periodic")):
+        w = oracle.stencil_weights(kind)
+        u = oracle.mapoverlap2d_f32(x, 1, w, boundary)
+        v, _ = oracle.chain_map_stencil_sumsq_f32("copy", x, 1, w, boundary)
+        assert v == pytest.approx(float(np.sum(u * u)), rel=1e-13)
+
+
+def test_chain_periodic_is_shift_invariant():
+    x = syn.uniform_f32(63, 17 * 24).reshape(17, 24)
+    w = syn.uniform_f32(64, 9, -1.0, 1.0).reshape(3, 3)
+    v0, _ = oracle.chain_map_stencil_sumsq_f32("tanh", x, 1, w, "periodic")
+    v1, _ = oracle.chain_map_stencil_sumsq_f32("tanh", np.roll(x, (5, -7), axis=(0, 1)), 1, w, "periodic")
+    assert v1 == pytest.approx(v0, rel=1e-13)
+
+
 # -------------------------------------------------------------- Generator ---
 def test_generator_published_splitmix64_values():
     """First outputs of SplitMix64 from seed 0 (Vigna's reference
