@@ -497,7 +497,8 @@ def config_legs(sk, torch, stream):
     from the step: dot at n = 2^20 (latency-bound, cold and warm L2), a
     10-call 9-point stencil chain on 8192^2 (composed vs one call per step),
     the batched instances as one CUDA-graph replay against 2 x 4096 separate
-    calls, forward + backward of the composed loss on 8192^2, and the host
+    calls, forward + backward of the composed loss on 8192^2, the composed
+    Map -> MapOverlap -> MapReduce chain per call and fused, and the host
     edge variants on host-resident inputs."""
     dev = torch.device("cuda")
     out = {}
@@ -590,6 +591,23 @@ def config_legs(sk, torch, stream):
     fwd_bwd()
     ms_ad = _event_ms(torch, stream, fwd_bwd, 5)
     out["autograd_8192sq"] = {"ms_fwd_bwd": round(ms_ad, 3)}
+    # the composed chain tanh -> 9-point stencil -> sum of squares, 8192^2,
+    # per call (three dispatched calls) against fused (one pass)
+    cxg = sk.Container.from_tensor(xg.detach())
+    rr = torch.zeros(1, device=dev)
+    crr = sk.Container.from_tensor(rr)
+    comp = {}
+    for vname, v in (("per_call", 0), ("fused", 1)):
+        sk.skel_force_variant("compose", v)
+        try:
+            fn = lambda: sk.skel_compose_map_stencil_sumsq("tanh", "stencil9", cxg, result_dev=crr, host=False)
+            fn()
+            comp[vname] = _event_ms(torch, stream, fn, 5)
+        finally:
+            sk.skel_force_variant("compose", -1)
+    out["compose_8192sq"] = {"ms_per_call": round(comp["per_call"], 3), "ms_fused": round(comp["fused"], 3),
+                             "speedup": round(comp["per_call"] / comp["fused"], 2),
+                             "fused_GB/s": round(4 * side * side / comp["fused"] / 1e6, 1)}
     out["host_edge_2e26"] = host_edge_leg(sk, torch, stream)
     return out
 

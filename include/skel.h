@@ -119,7 +119,8 @@ typedef enum {
     SKEL_SK_BATCHED = 7,
     SKEL_SK_CHAIN2D = 8,   /* a chain of 2D MapOverlap calls (skel_mapoverlap_chain) */
     SKEL_SK_EDGE = 9,      /* host edge of Map / Reduce / MapReduce calls on host-only inputs */
-    SKEL_SK_COUNT = 10
+    SKEL_SK_COMPOSE = 10,  /* Map -> MapOverlap -> MapReduce chain (skel_compose_map_stencil_sumsq) */
+    SKEL_SK_COUNT = 11
 } skel_skeleton;
 
 /* ------------------------------------------------------------ library --- */
@@ -305,6 +306,26 @@ int skel_mapoverlap(skel_fn fn, int radius, const float *weights, int nweights,
  * steps >= 1.  Enqueued on `stream`. */
 int skel_mapoverlap_chain(skel_fn fn, const float *weights, int nweights, skel_boundary boundary, int steps,
                           skel_handle in, skel_handle tmp, skel_handle out, void *stream);
+
+/* The chain Map -> MapOverlap -> MapReduce as one call (Sec. II: the
+ * implementation is selected for the composition, not call by call):
+ *   result = sum_{i,j} (S t)[i,j]^2,   t = map_fn(in)
+ * map_fn: TANH, SQ, SCALE (params[0] = a, nparams >= 1) or COPY; S: the 2D
+ * stencil of skel_mapoverlap (stencil = STENCIL5 or STENCIL9, radius 1,
+ * weights NULL or 9 values, boundary on t: outside a ZERO boundary t reads
+ * 0).  in: 2D F32.  The result (F32) goes to result_host (the call then
+ * waits) and/or to result_dev (a 1-element F32 container); at least one.
+ * Table key (SKEL_SK_COMPOSE, stencil, F32, n, radius 1, residency).
+ * Variants: per_call (the Map, MapOverlap and MapReduce calls, each
+ * dispatched as usual, through two n-element temporaries: 20 bytes of HBM
+ * traffic per point) and fused (tile 0..2: 32 << tile rows per block; one
+ * pass reading in once, 4 bytes per point, then one Reduce of the block
+ * partials; needs 16-byte aligned rows, cols % 4 == 0).  Both compute every
+ * stencil output with the same float32 operations; the sums differ in
+ * order only.  n = 0 gives 0. */
+int skel_compose_map_stencil_sumsq(skel_fn map_fn, const double *params, int nparams, skel_fn stencil,
+                                   const float *weights, int nweights, skel_boundary boundary, skel_handle in,
+                                   void *result_host, skel_handle result_dev, void *stream);
 
 /* MapArray: out[i] = f(A, B[i]) with A read whole (random access) and B per
  * element.  The paper does not define MapArray; the reading used is:

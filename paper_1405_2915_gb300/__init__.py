@@ -284,6 +284,20 @@ def skel_mapoverlap_chain(fn, weights, boundary, steps: int, x: Container, tmp, 
                                     _stream(stream)))
 
 
+def skel_compose_map_stencil_sumsq(map_fn, stencil, x: Container, params=(), weights=None, boundary="clamp",
+                                   result_dev: Container | None = None, host: bool = True, stream=None):
+    """sum_{i,j} (S map_fn(x))[i,j]^2 as one composed call (Map -> 2D
+    MapOverlap -> MapReduce); returns the value when host is True."""
+    res = np.zeros(1, dtype=np.float32)
+    p, np_ = _params(params)
+    w = _weights(weights)
+    check(lib.skel_compose_map_stencil_sumsq(_fn(map_fn), p, np_, _fn(stencil), w[0], w[1],
+                                             BOUNDARY[boundary] if isinstance(boundary, str) else boundary, x.handle,
+                                             C.c_void_p(res.ctypes.data) if host else None,
+                                             None if result_dev is None else result_dev.handle, _stream(stream)))
+    return res[0] if host else None
+
+
 def skel_maparray(fn, whole: Container, elem: Container, out: Container, stream=None) -> None:
     check(lib.skel_maparray(_fn(fn), whole.handle, elem.handle, out.handle, _stream(stream)))
 

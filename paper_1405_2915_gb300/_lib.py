@@ -22,7 +22,7 @@ BOUNDARY = {"clamp": 0, "zero": 1, "periodic": 2}
 READ, WRITE, READWRITE = 1, 2, 3
 UNIT_HOST, UNIT_DEVICE = 1, 2
 SK = {"map": 0, "reduce": 1, "mapreduce": 2, "scan": 3, "mapoverlap1d": 4, "mapoverlap2d": 5,
-      "maparray": 6, "batched": 7, "chain2d": 8, "edge": 9}
+      "maparray": 6, "batched": 7, "chain2d": 8, "edge": 9, "compose": 10}
 
 vp, i32, i64, dbl, f32p = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.POINTER(C.c_float)
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -55,6 +55,7 @@ SIGNATURES = {
     "skel_maparray": (i32, [i32, vp, vp, vp, vp]),
     "skel_mapoverlap_chain": (i32, [i32, f32p, i32, i32, i32, vp, vp, vp, vp]),
     "skel_maparray_grid": (i32, [i32, vp, vp, C.POINTER(dbl), i32, vp]),
+    "skel_compose_map_stencil_sumsq": (i32, [i32, C.POINTER(dbl), i32, i32, f32p, i32, i32, vp, vp, vp, vp]),
     "skel_batched": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp]),
     "skel_batched_plan_create": (i32, [i32, i32, i32, i32, vp, vp, vp, vp, vp, C.POINTER(vp)]),
     "skel_plan_launch": (i32, [vp, vp]),

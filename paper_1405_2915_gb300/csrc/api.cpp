@@ -998,6 +998,100 @@ int skel_mapoverlap_chain(skel_fn fn, const float *weights, int nweights, skel_b
     });
 }
 
+int skel_compose_map_stencil_sumsq(skel_fn map_fn, const double *params, int nparams, skel_fn stencil,
+                                   const float *weights, int nweights, skel_boundary boundary, skel_handle in,
+                                   void *result_host, skel_handle result_dev, void *stream)
+{
+    return guarded([&] {
+        if (map_fn != SKEL_FN_TANH && map_fn != SKEL_FN_SQ && map_fn != SKEL_FN_SCALE && map_fn != SKEL_FN_COPY)
+            return fail(SKEL_ERR_UNSUPPORTED, "composed chain: map must be TANH, SQ, SCALE or COPY");
+        if (map_fn == SKEL_FN_SCALE && (!params || nparams < 1))
+            return fail(SKEL_ERR_INVALID_ARG, "composed chain: SCALE needs params[0]");
+        if (stencil != SKEL_FN_STENCIL5 && stencil != SKEL_FN_STENCIL9)
+            return fail(SKEL_ERR_UNSUPPORTED, "composed chain: stencil must be STENCIL5 or STENCIL9");
+        if (!valid_handle(in)) return fail(SKEL_ERR_INVALID_ARG, "bad input handle");
+        if (in->ndim != 2 || in->dtype != SKEL_F32) return fail(SKEL_ERR_DTYPE, "composed chain: in must be 2D float32");
+        if (boundary < SKEL_CLAMP || boundary > SKEL_PERIODIC) return fail(SKEL_ERR_INVALID_ARG, "unknown boundary");
+        if (weights && nweights != 9) return fail(SKEL_ERR_SHAPE, "2D weights: need 9 values (3x3 row-major)");
+        if (!result_host && !result_dev) return fail(SKEL_ERR_INVALID_ARG, "no result destination");
+        if (result_dev && (!valid_handle(result_dev) || result_dev->n != 1 || result_dev->dtype != SKEL_F32))
+            return fail(SKEL_ERR_SHAPE, "result container must hold 1 float32 element");
+        if (result_dev && same_storage(result_dev, in)) return fail(SKEL_ERR_INVALID_ARG, "result aliases the input");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<Operand> ops{{in, SKEL_READ}};
+        if (result_dev) ops.push_back({result_dev, SKEL_WRITE});
+        int res = 0;
+        int rc = acquire_all(ops, s, &res);
+        if (rc) return rc;
+        void *out = nullptr;
+        if (result_dev) out = ops.back().ptr;
+        else if ((rc = result_slot(s, &out))) return rc;
+        const int64_t n = in->n;
+        std::vector<float> wbuf;
+        ComposeLaunch cl{map_fn, map_fn == SKEL_FN_SCALE ? (float)params[0] : 0.f, boundary,
+                         weights ? weights : default_weights(stencil, 1, wbuf), stencil == SKEL_FN_STENCIL5,
+                         static_cast<const float *>(ops[0].ptr), in->shape[0], in->shape[1]};
+        const Allocator rec = current_allocator();
+        // the sum of squares of the chain's last stage, over `len` values at v
+        auto sumsq = [&](const float *v, int64_t len, int map) {
+            ReduceLaunch r{SKEL_FN_ADD, map, SKEL_F32, v, nullptr, out, len};
+            const int sk = map < 0 ? (int)SKEL_SK_REDUCE : (int)SKEL_SK_MAPREDUCE;
+            Context c{sk, map < 0 ? (int)SKEL_FN_ADD : map, SKEL_F32, len, 0, 0};
+            return run_with_fallback(sk, c, [&](const Choice &cc) { return launch_reduce(r, cc, s); }, reduce_def);
+        };
+        if (n == 0) {   // the empty sum: 0
+            if ((rc = sumsq(nullptr, 0, SKEL_FN_SQ))) return rc;
+            return result_host ? copy_result_to_host(result_host, out, 4, s) : (int)SKEL_OK;
+        }
+        Context ctx{SKEL_SK_COMPOSE, stencil, SKEL_F32, n, 1, res};
+        rc = run_with_fallback(SKEL_SK_COMPOSE, ctx, [&](const Choice &c) -> int {
+            if (c.variant == 1) {
+                int64_t np = 0;
+                int r1 = compose_fused_check(cl, c, &np);
+                if (r1) return r1;
+                float *parts = static_cast<float *>(dev_alloc(rec, (size_t)np * 4, s));
+                if (!parts) return fail(SKEL_ERR_OOM, "composed chain: partial sums");
+                r1 = launch_compose_fused(cl, c, parts, s);
+                if (!r1) r1 = sumsq(parts, np, -1);
+                dev_free(rec, parts, s);
+                return r1;
+            }
+            if (c.variant != 0) return fail(SKEL_ERR_INVALID_ARG, "composed chain: unknown variant");
+            // per call: Map -> MapOverlap -> MapReduce(sq, +), each dispatched
+            float *t = static_cast<float *>(dev_alloc(rec, (size_t)n * 4, s));
+            float *u = t ? static_cast<float *>(dev_alloc(rec, (size_t)n * 4, s)) : nullptr;
+            int r1 = (t && u) ? (int)SKEL_OK : fail(SKEL_ERR_OOM, "composed chain: temporaries");
+            if (!r1) {
+                MapLaunch m{map_fn, cl.a, cl.in, nullptr, t, n};
+                Context cm{SKEL_SK_MAP, map_fn, SKEL_F32, n, 0, 0};
+                r1 = run_with_fallback(SKEL_SK_MAP, cm, [&](const Choice &cc) { return launch_map(m, cc, s); }, map_def);
+            }
+            if (!r1) {
+                StencilLaunch st{};
+                st.ndim = 2;
+                st.radius = 1;
+                st.boundary = boundary;
+                st.w = cl.w;
+                st.taps5 = cl.taps5;
+                st.in = t;
+                st.out = u;
+                st.rows = cl.rows;
+                st.cols = cl.cols;
+                st.transpose = false;
+                Context cs2{SKEL_SK_MAPOVERLAP2D, stencil, SKEL_F32, n, 1, 0};
+                r1 = run_with_fallback(SKEL_SK_MAPOVERLAP2D, cs2,
+                                       [&](const Choice &cc) { return launch_stencil(st, cc, s); }, st2_def);
+            }
+            if (!r1) r1 = sumsq(u, n, SKEL_FN_SQ);
+            if (u) dev_free(rec, u, s);
+            if (t) dev_free(rec, t, s);
+            return r1;
+        }, compose_default);
+        if (rc) return rc;
+        return result_host ? copy_result_to_host(result_host, out, 4, s) : (int)SKEL_OK;
+    });
+}
+
 int skel_maparray(skel_fn fn, skel_handle whole, skel_handle elem, skel_handle out, void *stream)
 {
     return guarded([&] {
@@ -1407,6 +1501,7 @@ int skel_variant_count(int skeleton)
     case SKEL_SK_BATCHED: return batched_variant_count();
     case SKEL_SK_CHAIN2D: return chain_variant_count();
     case SKEL_SK_EDGE: return 3;
+    case SKEL_SK_COMPOSE: return compose_variant_count();
     default: return 0;
     }
 }
@@ -1422,6 +1517,7 @@ const char *skel_variant_name(int skeleton, int variant)
     case SKEL_SK_MAPARRAY: return maparray_variant_name(variant);
     case SKEL_SK_BATCHED: return batched_variant_name(variant);
     case SKEL_SK_CHAIN2D: return chain_variant_name(variant);
+    case SKEL_SK_COMPOSE: return compose_variant_name(variant);
     case SKEL_SK_EDGE: {
         static const char *names[] = {"copy", "chunked", "direct"};
         return variant >= 0 && variant < 3 ? names[variant] : "?";

@@ -197,6 +197,24 @@ int stencil_variant_count(int ndim);
 const char *stencil_variant_name(int ndim, int v);
 Choice stencil_default(int ndim);
 
+// The composed chain Map -> MapOverlap (2D, radius 1) -> MapReduce(sq, +),
+// fused into one pass over x (variant 1 of SKEL_SK_COMPOSE).
+struct ComposeLaunch {
+    int map_fn;          // SKEL_FN_TANH / SQ / SCALE / COPY
+    float a;             // the map's parameter (SCALE)
+    int boundary;
+    const float *w;      // 9 weights, host copy (row-major 3x3)
+    int taps5;
+    const float *in;
+    int64_t rows, cols;
+};
+// Checks the fused variant's constraints; *nparts: the partial sums it writes.
+int compose_fused_check(const ComposeLaunch &cl, const Choice &c, int64_t *nparts);
+int launch_compose_fused(const ComposeLaunch &cl, const Choice &c, float *partials, cudaStream_t s);
+int compose_variant_count();
+const char *compose_variant_name(int v);
+Choice compose_default();
+
 // MapArray over a grid (fn COULOMB): atoms (m x 4 float32: x, y, z, q),
 // out rows x cols, grid position of out[i, j] = (j*h, i*h, z0).
 struct CoulombLaunch {

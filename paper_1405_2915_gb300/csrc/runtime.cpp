@@ -287,6 +287,7 @@ Choice builtin_default(int sk)
     case SKEL_SK_MAPARRAY: return maparray_default();
     case SKEL_SK_BATCHED: return batched_default();
     case SKEL_SK_CHAIN2D: return chain_default();
+    case SKEL_SK_COMPOSE: return compose_default();
     default: return Choice{0, 0, 0, 0};
     }
 }

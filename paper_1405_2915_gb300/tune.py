@@ -30,7 +30,7 @@ import torch
 
 from . import (F32, I32, SK, UNIT_HOST, Container, SkelError, skel_batched, skel_force_variant, skel_load_dispatch_table,
                skel_map, skel_mapoverlap, skel_mapoverlap_chain, skel_maparray, skel_maparray_grid, skel_mapreduce,
-               skel_reduce, skel_scan, skel_scan_bwd)
+               skel_reduce, skel_scan, skel_scan_bwd, skel_compose_map_stencil_sumsq)
 from ._lib import FN
 
 L2_FLUSH_BYTES = 512 << 20
@@ -105,6 +105,10 @@ def candidates(sk_name: str):
         yield (0, 0, 0, 0)
         for k in (1, 2, 3, 4, 5, 6, 8):
             yield (1, 256, 0, k)
+    elif sk_name == "compose":
+        yield (0, 0, 0, 0)
+        for t in (0, 1, 2):      # fused: 32, 64, 128 rows per block
+            yield (1, 0, 0, t)
     elif sk_name == "edge":
         yield (0, 0, 0, 0)
         for t in (0, 1, 2):      # chunks of 8, 32, 128 MiB
@@ -117,6 +121,14 @@ def candidates(sk_name: str):
         yield (3, 256, 4, 0)
         yield (5, 256, 4, 0)
         yield (5, 256, 8, 0)
+
+
+def grid_side(n: int) -> int:
+    """The side of the square grid that stands for n points: sqrt(n) rounded
+    to a multiple of 4, so that a grid of about 2n points (the second timing
+    point of a bucket) keeps 16-byte aligned rows like the bucket's own
+    4^k-point grid, and no variant that needs them is ruled out there."""
+    return max(4, 4 * int(round(n ** 0.5 / 4)))
 
 
 class Instance:
@@ -218,7 +230,7 @@ def instances(nmax_log2: int):
         bufs = {}
 
         def make(n):
-            side = int(round(n ** 0.5))
+            side = grid_side(n)
             if "x" not in bufs:
                 bufs["x"], bufs["o"] = vec(nmax, 0.0, 1.0), vec(nmax)
             x = Container.from_tensor(bufs["x"][:side * side].view(side, side))
@@ -234,7 +246,7 @@ def instances(nmax_log2: int):
         bufs = {}
 
         def make(n):
-            side = int(round(n ** 0.5))
+            side = grid_side(n)
             if "x" not in bufs:
                 bufs["x"], bufs["o"], bufs["t"] = vec(nmax, 0.0, 1.0), vec(nmax), vec(nmax)
             x, o, t = (Container.from_tensor(bufs[k][:side * side].view(side, side)) for k in ("x", "o", "t"))
@@ -244,6 +256,21 @@ def instances(nmax_log2: int):
     for fn in ("stencil9", "stencil5"):
         out.append(Instance(f"mapoverlap2d chain {fn} clamp x10", "chain2d", FN[fn], F32, 10, nmax, mk_chain(fn, 10),
                             lambda n: 80 * n, sizes))
+
+    def mk_compose(fn, map_fn):   # Map -> MapOverlap -> MapReduce(sq, +), one call
+        bufs = {}
+
+        def make(n):
+            side = grid_side(n)
+            if "x" not in bufs:
+                bufs["x"], bufs["r"] = vec(nmax), torch.zeros(1, device=dev)
+            x = Container.from_tensor(bufs["x"][:side * side].view(side, side))
+            r = Container.from_tensor(bufs["r"])
+            return lambda: skel_compose_map_stencil_sumsq(map_fn, fn, x, result_dev=r, host=False)
+        return make
+
+    out.append(Instance("compose tanh -> stencil9 -> sumsq", "compose", FN["stencil9"], F32, 1, nmax,
+                        mk_compose("stencil9", "tanh"), lambda n: 4 * n, sizes))
 
     def mk_st1(r):
         bufs = {}

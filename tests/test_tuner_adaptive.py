@@ -45,3 +45,15 @@ def test_several_changes_are_all_found():
 def test_empty_and_single():
     assert tune.adaptive_sizes([], lambda n: 1, key=lambda r: r) == {}
     assert tune.adaptive_sizes([5], lambda n: "x", key=lambda r: r) == {5: "x"}
+
+
+def test_grid_sides_keep_aligned_rows():
+    """Both timing points of a 2D bucket (4^k and about 2 * 4^k points) are
+    square grids with a multiple of 4 columns; the side is off sqrt(n) by at
+    most 2, so the point count by at most 4 sqrt(n) + 4."""
+    for k in range(5, 15):
+        for n in (4 ** k, 2 * 4 ** k):
+            side = tune.grid_side(n)
+            assert side % 4 == 0
+            assert abs(side * side - n) <= 4 * n ** 0.5 + 4
+        assert tune.grid_side(4 ** k) == 2 ** k
