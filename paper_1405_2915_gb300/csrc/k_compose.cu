@@ -46,9 +46,13 @@ compose_colwalk(const float *__restrict__ in, int64_t rows, int64_t cols, int b,
         // the last lane of the row) the neighbour column outside the warp's
         // strip, all loads issued together and nothing waiting on them;
         // cells outside a ZERO boundary stay 0.
+        constexpr int U = 4;
+        // every row this warp loads lies in [r0 - 1, r1 + U - 1]; a block
+        // whose rows are all inside the grid needs no boundary map for rows
+        const bool interior = r0 >= 1 && r1 + U <= rows;   // block-uniform
         auto load = [&](int64_t r) {
             Row6 v{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const int64_t gr = bmap(r, rows, b);
+            const int64_t gr = interior ? r : bmap(r, rows, b);
             if (gr >= 0 && active) {
                 const float *row = in + gr * cols;
                 const float4 q = dev::ld_stream(reinterpret_cast<const float4 *>(row + c0));
@@ -73,7 +77,6 @@ compose_colwalk(const float *__restrict__ in, int64_t rows, int64_t cols, int b,
         finish(m);
         // batches of U rows, the next batch's loads in flight while the
         // current one is computed
-        constexpr int U = 4;
         Row6 cur[U], nxt[U] = {};
 #pragma unroll
         for (int u = 0; u < U; ++u) cur[u] = load(r0 + 1 + u);   // rows past r1 are loaded but unused
