@@ -135,13 +135,15 @@ const char *skel_last_error(void);
 /* Device memory allocator used for container storage and kernel scratch.
  * alloc(bytes, stream, ctx) returns device memory usable on `stream` or NULL;
  * free(ptr, stream, ctx) releases it (stream-ordered).  Passing NULL for
- * alloc restores the built-in allocator (cudaMallocAsync / cudaFreeAsync).
+ * alloc restores the built-in allocator (cudaMallocFromPoolAsync on the library's own pool / cudaFreeAsync).
  * Containers and scratch already allocated keep the allocator they were
  * allocated with.  Not thread-safe against concurrent skeleton calls. */
 int skel_set_allocator(void *(*alloc)(size_t bytes, void *stream, void *ctx),
                        void (*free_fn)(void *ptr, void *stream, void *ctx), void *ctx);
 
-/* Releases the cached scratch memory and result slots of every stream.
+/* Releases the cached scratch memory and result slots of every stream, and
+ * returns the unused memory of the built-in allocator's pools (the library
+ * keeps its own pool per device, which holds freed memory for later calls).
  * Containers are not touched.  Waits for the streams that used them. */
 int skel_release_cached(void);
 

@@ -83,12 +83,48 @@ void set_allocator(const Allocator &a)
     g_alloc = a;
 }
 
+// The built-in allocator draws from a memory pool of the library's own on
+// each device, with no release threshold: what a call frees stays with the
+// pool for the next call.  (The device's default pool hands freed memory
+// back at every synchronisation, so a call with large temporaries, such as
+// the per-call composed chain, would have them mapped again each time.)
+// skel_release_cached() returns the pools' unused memory.
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64] = {};
+
+static cudaMemPool_t own_pool()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        g_pool[dev] = pool;
+    }
+    return g_pool[dev];
+}
+
 void *dev_alloc(const Allocator &a, size_t bytes, cudaStream_t stream)
 {
     if (bytes == 0) bytes = 256;
     if (a.alloc) return a.alloc(bytes, (void *)stream, a.ctx);
     void *p = nullptr;
-    if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
+    cudaMemPool_t pool = own_pool();
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, stream) : cudaMallocAsync(&p, bytes, stream);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -221,6 +257,9 @@ int release_scratch()
     cudaSetDevice(cur);
     g_scratch.clear();
     g_slots.clear();
+    std::lock_guard<std::mutex> lp(g_pool_mu);
+    for (cudaMemPool_t pool : g_pool)
+        if (pool) cudaMemPoolTrimTo(pool, 0);   // memory no allocation holds goes back
     return SKEL_OK;
 }
 
