@@ -57,3 +57,15 @@ def test_grid_sides_keep_aligned_rows():
             assert side % 4 == 0
             assert abs(side * side - n) <= 4 * n ** 0.5 + 4
         assert tune.grid_side(4 ** k) == 2 ** k
+
+
+def test_tuner_tries_every_variant_the_library_offers():
+    """The off-line tuner's candidate list of each skeleton covers exactly the
+    variants the library reports (a variant the tuner never times can never
+    enter the execution-plan table)."""
+    import paper_1405_2915_gb300 as sk
+    for name in sk.SK:
+        offered = set(range(sk.skel_variant_count(name)))
+        tried = {c[0] for c in tune.candidates(name)}
+        assert tried == offered, (name, sorted(tried), sorted(offered))
+        assert all(sk.skel_variant_name(name, v) != "?" for v in offered)
