@@ -26,7 +26,7 @@ namespace {
 struct Row6 { float l, x0, x1, x2, x3, r; };
 
 template <bool TAPS5, int FN, int RH>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, 5)
 compose_colwalk(const float *__restrict__ in, int64_t rows, int64_t cols, int b, W9 w, float a,
                 float *__restrict__ partials)
 {
