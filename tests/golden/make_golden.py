@@ -41,6 +41,18 @@ def cases():
     yield "mapoverlap2d_5pt_clamp", oracle.mapoverlap2d_f32(g, 1, w5, "clamp").ravel()
     yield "mapoverlap2d_9pt_clamp_bwd", oracle.mapoverlap2d_bwd_f32(g, 1, w9, "clamp").ravel()
     yield "composed_loss_grad", oracle.composed_loss_f32(g, 1, w9, "clamp")[1].ravel()
+    yield "mapoverlap2d_chain_9pt_zero_x3", oracle.mapoverlap2d_chain_f32(g, 1, w9, "zero", 3).ravel()
+    yield "chain_tanh_9pt_sumsq_periodic", np.array(oracle.chain_map_stencil_sumsq_f32("tanh", g, 1, w9, "periodic"))
+    M = syn.uniform_f32(106, 5 * 37).reshape(5, 37)
+    yield "maparray_rowdot", oracle.rowdot_f32(x, M)[0]
+    idx = syn.uniform_int(107, 11, 0, 36)
+    yield "maparray_gather", oracle.gather_f32(x, idx)
+    atoms = syn.uniform_f32(108, 3 * 4, 0.0, 1.0).reshape(3, 4)
+    yield "coulomb_points", oracle.coulomb_points_f32(atoms, np.array([0, 2, 5]), np.array([1, 0, 3]), 0.25, -1.0)[0]
+    off = np.array([0, 0, 5, 6, 37], np.int64)
+    sumsq, scan, _ = oracle.batched_f32(x, off, True)
+    yield "batched_sumsq", sumsq
+    yield "batched_scan_incl", scan
 
 
 def main():
