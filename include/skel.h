@@ -268,11 +268,16 @@ int skel_scan(skel_fn op, int inclusive, skel_handle in, skel_handle out, void *
  * exits.  n must be <= SKEL_SCAN_NOALLOC_MAX_N (2^27, the array's capacity);
  * larger n returns SKEL_ERR_SHAPE without launching.  The first call on each
  * device looks up the array's device address and clears it (stream-ordered
- * on `stream`); make that first call before any stream capture.  Every call
- * shares the array and each leaves it ready for the next, so calls that
- * overlap on the GPU (on two streams at once, or from two threads) race on
- * it and must be serialised by the caller.  Enqueued on `stream`; returns
- * without waiting. */
+ * on `stream`); make that first call before any stream capture.  The array
+ * also holds the tag that marks which call wrote a look-back word: the
+ * kernel reads it, and its last block to finish advances it (clearing the
+ * words every 255 calls), so consecutive calls need nothing from the host
+ * besides the address.  Every call shares the array and each leaves it ready
+ * for the next, so calls that overlap on the GPU (on two streams at once, or
+ * from two threads) race on it and must be serialised by the caller.  A
+ * bounded look-back wait that gives up (skel_set_debug key 2) is recorded in
+ * the array and reported, and cleared, by the next skel_check_device on this
+ * device, as for skel_scan.  Enqueued on `stream`; returns without waiting. */
 #define SKEL_SCAN_NOALLOC_MAX_N ((int64_t)1 << 27)
 int skel_scan_noalloc(skel_fn op, int inclusive, skel_dtype dtype, const void *in, void *out, int64_t n,
                       void *stream);
@@ -475,8 +480,10 @@ const char *skel_variant_name(int skeleton, int variant);
 /* ---------------------------------------------------- device status ---- */
 
 /* Waits for `stream` and reports device-side failures of the calls made on
- * it since the last check: SKEL_ERR_TIMEOUT if a bounded wait (the scan's
- * look-back over predecessor tiles, a TMA copy) gave up, SKEL_ERR_INVALID_ARG
+ * it since the last check (and of skel_scan_noalloc calls on the current
+ * device, whose status sits in its static array): SKEL_ERR_TIMEOUT if a
+ * bounded wait (the scan's look-back over predecessor tiles, a TMA copy)
+ * gave up, SKEL_ERR_INVALID_ARG
  * if a batched call found its device-resident offsets invalid (that call
  * computed nothing), SKEL_OK otherwise.  Clears the recorded status. */
 int skel_check_device(void *stream);

@@ -1533,12 +1533,17 @@ int skel_check_device(void *stream)
     return guarded([&] {
         cudaStream_t s = (cudaStream_t)stream;
         SKEL_CUDA_TRY(cudaStreamSynchronize(s));
-        Control *ctl = scratch_control(s);
-        if (!ctl) return (int)SKEL_OK;
         uint32_t err = 0;
-        SKEL_CUDA_TRY(cudaMemcpy(&err, &ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+        if (Control *ctl = scratch_control(s)) {
+            SKEL_CUDA_TRY(cudaMemcpy(&err, &ctl->error, sizeof(err), cudaMemcpyDeviceToHost));
+            if (err) SKEL_CUDA_TRY(cudaMemset(&ctl->error, 0, sizeof(uint32_t)));
+        }
+        // the allocation-free scan records into its own static control block
+        uint32_t err_static = 0;
+        int rc = noalloc_take_status(&err_static);
+        if (rc) return rc;
+        err |= err_static;
         if (err) {
-            SKEL_CUDA_TRY(cudaMemset(&ctl->error, 0, sizeof(uint32_t)));
             if (err & kErrTimeout)
                 return fail(SKEL_ERR_TIMEOUT, "a bounded device wait (scan look-back) gave up; results of that call are invalid");
             if (err & kErrInput)

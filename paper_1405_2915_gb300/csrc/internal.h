@@ -48,7 +48,8 @@ struct Control {
     uint32_t abort;      // epoch of a call whose bounded wait gave up; its other waiters stop
     uint32_t queue;      // work queue of persistent kernels
     uint32_t exited;     // persistent blocks that left the work loop
-    uint32_t pad[58];
+    uint32_t epoch;      // last look-back tag of a kernel that keeps its tag on the device (0: none yet)
+    uint32_t pad[57];
 };
 static_assert(sizeof(Control) == 256, "control block is 256 bytes");
 constexpr uint32_t kErrTimeout = 1u;   // a bounded wait gave up
@@ -73,6 +74,11 @@ int get_scratch(cudaStream_t stream, size_t data_bytes, size_t word_count, Scrat
 // Control block of the scratch of `stream`, or nullptr if none was made.
 Control *scratch_control(cudaStream_t stream);
 int release_scratch();
+// Device status bits recorded by the allocation-free scan on the current
+// device (its control block lives in a static array, not in a stream's
+// scratch); *err = 0 if that entry point never ran on this device.  Clears
+// them.  Synchronous.
+int noalloc_take_status(uint32_t *err);
 // Fixed 256-byte device buffer of `stream` for scalar results.
 int result_slot(cudaStream_t stream, void **out);
 
