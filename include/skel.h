@@ -226,7 +226,11 @@ int skel_coherence_step(int valid_units, int unit, int mode, int *new_valid, int
  * fn: ADD, SUB, MUL, MAX (2 inputs); AXPY (2 inputs, params[0] = a);
  *     TANH, SQ, COPY (1 input); SCALE (1 input, params[0] = a).
  * All operands SKEL_F32 with the same element count (shapes may differ).
- * out may be the same container as an input (in-place). */
+ * out may be the same container as an input, or another container over the
+ * same device memory (in place: every variant then runs without the
+ * read-only load path).  An output that shares only part of an input's
+ * bytes (a shifted view, or a wrapped pointer into it) returns
+ * SKEL_ERR_INVALID_ARG before any copy or launch. */
 int skel_map(skel_fn fn, const double *params, int nparams, const skel_handle *ins, int nin,
              skel_handle out, void *stream);
 

@@ -425,6 +425,26 @@ bool overlaps(skel_handle a, skel_handle b)
     return a0 < b1 && b0 < a1;
 }
 
+// Whether the device copies of a and b share bytes: views of one storage by
+// their offsets, distinct storages (two containers wrapping the same device
+// memory) by their device addresses.  *exact: both start at one address.
+bool device_overlap(skel_handle a, skel_handle b, bool *exact)
+{
+    *exact = false;
+    if (a->n == 0 || b->n == 0) return false;
+    if (same_storage(a, b)) {
+        const bool o = overlaps(a, b);
+        *exact = o && a->offset == b->offset;
+        return o;
+    }
+    if (!a->st->dev || !b->st->dev) return false;
+    const char *a0 = static_cast<const char *>(a->st->dev) + a->offset, *a1 = a0 + a->n * dtype_size(a->dtype);
+    const char *b0 = static_cast<const char *>(b->st->dev) + b->offset, *b1 = b0 + b->n * dtype_size(b->dtype);
+    const bool o = a0 < b1 && b0 < a1;
+    *exact = o && a0 == b0;
+    return o;
+}
+
 template <class Launch>
 int run_with_fallback(int sk, const Context &ctx, Launch launch, Choice (*def)())
 {
@@ -663,6 +683,7 @@ int map_edge(int fn, float a, const skel_handle *ins, int nin, skel_handle out, 
     float *o = (float *)po;
     auto run = [&](int64_t off, int64_t len, int res) {
         MapLaunch m{fn, a, i0 + off, i1 ? i1 + off : nullptr, o + off, len};
+        m.alias = i0 == o || (i1 && i1 == o);
         Context ctx{SKEL_SK_MAP, fn, SKEL_F32, len, 0, res};
         return run_with_fallback(SKEL_SK_MAP, ctx, [&](const Choice &c) { return launch_map(m, c, s); }, map_def);
     };
@@ -841,7 +862,8 @@ int skel_map(skel_fn fn, const double *params, int nparams, const skel_handle *i
             if (!valid_handle(ins[k])) return fail(SKEL_ERR_INVALID_ARG, "bad input handle");
             if (ins[k]->dtype != SKEL_F32) return fail(SKEL_ERR_DTYPE, "map: float32 only");
             if (ins[k]->n != out->n) return fail(SKEL_ERR_SHAPE, "map: operands differ in length");
-            if (overlaps(ins[k], out) && !(ins[k]->offset == out->offset))
+            bool exact = false;
+            if (device_overlap(ins[k], out, &exact) && !exact)
                 return fail(SKEL_ERR_INVALID_ARG, "map: output partially overlaps an input");
         }
         if (out->dtype != SKEL_F32) return fail(SKEL_ERR_DTYPE, "map: float32 only");
@@ -871,6 +893,7 @@ int skel_map(skel_fn fn, const double *params, int nparams, const skel_handle *i
         if (rc) return rc;
         MapLaunch m{fn, a, (const float *)ops[0].ptr,
                     nin == 2 ? (const float *)ops[1].ptr : nullptr, (float *)ops.back().ptr, out->n};
+        m.alias = m.in0 == m.out || (m.in1 && m.in1 == m.out);
         Context ctx{SKEL_SK_MAP, fn, SKEL_F32, out->n, 0, res};
         return run_with_fallback(SKEL_SK_MAP, ctx, [&](const Choice &c) { return launch_map(m, c, s); }, map_def);
     });

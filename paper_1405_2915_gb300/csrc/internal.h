@@ -147,6 +147,7 @@ struct MapLaunch {
     const float *in1;
     float *out;
     int64_t n;
+    bool alias = false;  // out is in0 or in1 (in place): no restrict, coherent loads
 };
 int launch_map(const MapLaunch &m, const Choice &c, cudaStream_t s);
 int map_variant_count();

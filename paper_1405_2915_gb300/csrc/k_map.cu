@@ -10,6 +10,12 @@
 // Variants 1-3 need every operand at the same address offset modulo 16 bytes;
 // the few elements before the first 16-byte boundary and after the last full
 // float4 are handled by scalar threads of the same launch.
+//
+// In-place calls (out is one of the inputs, m.alias) run each variant's
+// access pattern in kernels without __restrict__ and with plain coherent
+// loads and stores: the read-only (non-coherent) load path and restrict
+// qualifiers both promise that no memory the kernel reads is written during
+// the kernel, which an in-place map breaks.
 #include "common.cuh"
 
 namespace skel {
@@ -111,6 +117,51 @@ __global__ void map_vec_grid(const float *__restrict__ x, const float *__restric
     }
 }
 
+// In-place forms (no __restrict__, coherent loads).  Every element is read
+// and then written by the same thread, so the result equals the out-of-place
+// one element for element.
+template <int FN>
+__global__ void map_scalar_inplace(const float *x, const float *y, float *out, int64_t n, float a)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        float yv = MapF<FN>::nin == 2 ? y[i] : 0.f;
+        out[i] = MapF<FN>::f(x[i], yv, a);
+    }
+}
+
+template <int FN, int EPT>
+__global__ void map_vec_inplace(const float *x, const float *y, float *out, int head, int64_t nvec, int tail,
+                                float a)
+{
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    map_edges<FN>(x, y, out, head, nvec, tail, a, gtid);
+    const float4 *x4 = reinterpret_cast<const float4 *>(x + head);
+    const float4 *y4 = reinterpret_cast<const float4 *>(y + head);
+    float4 *o4 = reinterpret_cast<float4 *>(out + head);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * EPT;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * EPT + threadIdx.x; base < nvec; base += step) {
+        float4 vx[EPT], vy[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            int64_t i = base + (int64_t)k * blockDim.x;
+            if (i < nvec) {
+                vx[k] = x4[i];
+                if (MapF<FN>::nin == 2) vy[k] = y4[i];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+            int64_t i = base + (int64_t)k * blockDim.x;
+            if (i < nvec) {
+                float4 q = vx[k], r = MapF<FN>::nin == 2 ? vy[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+                o4[i] = make_float4(MapF<FN>::f(q.x, r.x, a), MapF<FN>::f(q.y, r.y, a), MapF<FN>::f(q.z, r.z, a),
+                                    MapF<FN>::f(q.w, r.w, a));
+            }
+        }
+    }
+}
+
 template <int FN>
 int run_map(const MapLaunch &m, const Choice &c, cudaStream_t s)
 {
@@ -122,7 +173,8 @@ int run_map(const MapLaunch &m, const Choice &c, cudaStream_t s)
         const int64_t cap = (int64_t)device_info().sms * (2048 / block) * 4;
         if (grid > cap) grid = cap;
         if (grid < 1) grid = 1;
-        launch_kernel(map_scalar<FN>, (unsigned)grid, block, 0, s, m.in0, m.in1, m.out, m.n, a);
+        if (m.alias) launch_kernel(map_scalar_inplace<FN>, (unsigned)grid, block, 0, s, m.in0, m.in1, m.out, m.n, a);
+        else launch_kernel(map_scalar<FN>, (unsigned)grid, block, 0, s, m.in0, m.in1, m.out, m.n, a);
         return cudaPeekAtLastError() == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "map_scalar");
     }
     // vectorised variants: same offset modulo 16 bytes for every operand
@@ -148,7 +200,8 @@ int run_map(const MapLaunch &m, const Choice &c, cudaStream_t s)
     const unsigned g = (unsigned)grid;
 #define SKEL_MAP_EPT(E)                                                                          \
     do {                                                                                         \
-        if (c.variant == 1) launch_kernel(map_vec<FN, E, false>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
+        if (m.alias) launch_kernel(map_vec_inplace<FN, E>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
+        else if (c.variant == 1) launch_kernel(map_vec<FN, E, false>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
         else if (c.variant == 2) launch_kernel(map_vec<FN, E, true>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
         else launch_kernel(map_vec_grid<FN, E>, g, block, 0, s, m.in0, m.in1, m.out, (int)head, nvec, tail, a); \
     } while (0)

@@ -59,6 +59,44 @@ def test_map_in_place_and_mismatched_alignment():
     assert sk.skel_last_variant("map")[0] == 0
 
 
+@pytest.mark.parametrize("variant,block,ept", MAP_CONFIGS)
+@pytest.mark.parametrize("same_container", [True, False])
+@pytest.mark.parametrize("which", [0, 1])
+def test_map_in_place_every_variant(variant, block, ept, same_container, which):
+    """out is input `which` at the same alignment (the vector variants apply):
+    either the same container, or a second container wrapping the same
+    device memory.  Results equal the oracle's for every forced variant."""
+    sk = skel()
+    n = 1_000_003
+    x, y = syn.uniform_f32(23, n), syn.uniform_f32(24, n)
+    dx, dy = dev_tensor(x, 1), dev_tensor(y, 1)       # equal offsets modulo 16 bytes
+    cx, cy = wrap(dx), wrap(dy)
+    target = (dx, cx) if which == 0 else (dy, cy)
+    cout = target[1] if same_container else wrap(target[0])
+    with forced("map", variant, block, ept):
+        sk.skel_map("axpy", [cx, cy], cout, params=[2.5])
+        assert sk.skel_last_variant("map")[0] == variant
+    assert_elem_close(to_np(target[0]), oracle.map_f32("axpy", x, y, a=2.5), f"in-place axpy into input {which}")
+
+
+def test_map_partial_overlap_is_rejected():
+    import torch
+    sk = skel()
+    n = 4096
+    base = torch.zeros(n + 8, device="cuda")
+    a, b = base[:n], base[3:n + 3]                   # two wrapped pointers, 3 elements apart
+    ca = wrap(a)
+    with pytest.raises(sk.SkelError) as e:
+        sk.skel_map("scale", [ca], wrap(b), params=[2.0])
+    assert e.value.code == -1
+    parent = sk.Container.from_tensor(base)         # views of one container, shifted
+    v0, v1 = parent.view(0, (n,)), parent.view(5, (n,))
+    with pytest.raises(sk.SkelError) as e:
+        sk.skel_map("scale", [v0], v1, params=[2.0])
+    assert e.value.code == -1
+    v0.close(); v1.close()
+
+
 def test_map_empty_is_noop():
     import torch
     sk = skel()
