@@ -131,14 +131,69 @@ class ScanFn(torch.autograd.Function):
         return gin, None
 
 
-def composed_loss(x: torch.Tensor, weights=None, boundary: str = "clamp") -> torch.Tensor:
-    """The differentiable composed pipeline on a rows x cols grid:
-        t = tanh(x)                         Map
-        L1 = sum (S9 t)^2                   MapOverlap, MapReduce
-        C  = sum (rowscan t)^2              Scan (per row), MapReduce
-        L  = C / (rows * cols) + L1         Map (axpy on the two scalars)
-    Every step, forward and backward, is a skeleton call."""
-    t = MapFn.apply("tanh", 0.0, x)
-    l1 = SumSqFn.apply(MapOverlapFn.apply(t, "stencil9", 1, weights, boundary))
-    c = SumSqFn.apply(ScanFn.apply(t, True))
-    return MapFn.apply("axpy", 1.0 / x.numel(), c, l1)
+def _call(step, name: str, fn) -> None:
+    if step is None:
+        fn()
+    else:
+        step(name, fn)
+
+
+class ComposedLossFn(torch.autograd.Function):
+    """The differentiable composed pipeline as one Function, so that the
+    gradients of its two branches (t feeds both the stencil and the row scan)
+    are added by a skeleton call instead of by torch's autograd engine.
+
+    Forward (skeleton calls):
+        t = tanh(x)                              Map
+        u = S t, l1 = sum u^2                    MapOverlap, MapReduce(sq, +)
+        s = rowscan t, c = sum s^2               Scan (per row), MapReduce(sq, +)
+        L = c / (rows * cols) + l1               Map (axpy on the two scalars)
+    Backward, with g = dL (a device scalar):
+        gc = g / (rows * cols)                   Map (scale on the scalar)
+        gt = S^T (2 u g)                         MapReduce adjoint, transposed stencil
+        gt += rscan(2 s gc)                      MapReduce adjoint, reverse scan, Map (add, in place)
+        gx = gt (1 - t^2)                        Map adjoint of tanh (from the saved t)
+    `step(name, thunk)`, when given, runs each call (the benchmark times
+    them one by one); the calls and their order are the same either way."""
+
+    @staticmethod
+    def forward(ctx, x, weights, boundary: str, step=None):
+        x = _prep(x)
+        t, u, s = torch.empty_like(x), torch.empty_like(x), torch.empty_like(x)
+        r = torch.empty(2, device=x.device, dtype=torch.float32)     # l1, c
+        L = torch.empty(1, device=x.device, dtype=torch.float32)
+        ct, cu, cs = _c(t), _c(u), _c(s)
+        cl1, cc, cL = _c(r[0:1]), _c(r[1:2]), _c(L)
+        _call(step, "fwd_map_tanh", lambda: skel_map("tanh", [_c(x)], ct))
+        _call(step, "fwd_mapoverlap_9pt", lambda: skel_mapoverlap("stencil9", 1, weights, boundary, ct, cu))
+        _call(step, "fwd_sumsq_stencil", lambda: skel_mapreduce("sq", "add", [cu], result_dev=cl1, host=False))
+        _call(step, "fwd_row_scan", lambda: skel_scan("add", True, ct, cs))
+        _call(step, "fwd_sumsq_scan", lambda: skel_mapreduce("sq", "add", [cs], result_dev=cc, host=False))
+        _call(step, "fwd_combine", lambda: skel_map("axpy", [cc, cl1], cL, [1.0 / x.numel()]))
+        ctx.save_for_backward(t, u, s)
+        ctx.args = (weights, boundary, step, x.numel())
+        return L
+
+    @staticmethod
+    def backward(ctx, g):
+        t, u, s = ctx.saved_tensors
+        weights, boundary, step, n = ctx.args
+        g = _prep(g.reshape(1))
+        gc = torch.empty(1, device=g.device, dtype=torch.float32)
+        gu, gt, gs, gt2, gx = (torch.empty_like(t) for _ in range(5))
+        cg, cgc, cgt = _c(g), _c(gc), _c(gt)
+        _call(step, "bwd_scale", lambda: skel_map("scale", [cg], cgc, [1.0 / n]))
+        _call(step, "bwd_sumsq_stencil", lambda: skel_mapreduce_bwd("sq", "add", [_c(u)], cg, [_c(gu)]))
+        _call(step, "bwd_mapoverlap_9pt", lambda: skel_mapoverlap_bwd("stencil9", 1, weights, boundary, _c(gu), cgt))
+        _call(step, "bwd_sumsq_scan", lambda: skel_mapreduce_bwd("sq", "add", [_c(s)], cgc, [_c(gs)]))
+        _call(step, "bwd_reverse_scan", lambda: skel_scan_bwd("add", True, _c(gs), _c(gt2)))
+        _call(step, "bwd_add", lambda: skel_map("add", [cgt, _c(gt2)], cgt))
+        _call(step, "bwd_map_tanh", lambda: skel_map_bwd("tanh", [_c(t)], cgt, [_c(gx)], [1.0]))
+        return gx, None, None, None
+
+
+def composed_loss(x: torch.Tensor, weights=None, boundary: str = "clamp", step=None) -> torch.Tensor:
+    """L = sum (S9 tanh x)^2 + sum (rowscan tanh x)^2 / (rows * cols) on a
+    rows x cols grid (ComposedLossFn); every step, forward and backward, is a
+    skeleton call of libskel.so."""
+    return ComposedLossFn.apply(x, weights, boundary, step)
