@@ -172,6 +172,19 @@ class Workload:
         ]
 
 
+    def extra_calls(self):
+        """Calls outside the step that profiling runs may name with --only:
+        the ten-step 9-point chain (composed, as the table chooses it) and
+        the fused Map -> MapOverlap -> MapReduce chain, on the step's grid."""
+        sk, c, n = self.sk, self.c, N
+        return [
+            ("chain_9pt_x10", 8 * n * 10,
+             lambda: sk.skel_mapoverlap_chain("stencil9", None, "clamp", 10, c["grid"], c["oG2"], c["oG"])),
+            ("compose_tanh_9pt", 4 * n,
+             lambda: sk.skel_compose_map_stencil_sumsq("tanh", "stencil9", c["grid"], result_dev=c["r1"], host=False)),
+        ]
+
+
 def run_steps(torch, calls, steps, stream, per_call=True):
     """Runs `steps` steps; returns (total ms, {name: summed ms})."""
     E = torch.cuda.Event
@@ -288,8 +301,79 @@ def reference_sample(n_steps: int, budget_s: float = 150.0, cap_s: float = 8.0) 
 def cpu_baseline(sample: int = 1 << 25):
     dt, nb = oracle_sample_step(sample)
     return {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "cpu_model": host_model(),
             "sample": f"every skeleton of the step on n = {sample} elements (float64 oracle, one thread), "
                       f"{dt:.1f} s"}
+
+
+# ------------------------------------------------ parallel CPU baseline --
+def cpu_parallel_leg(sample_log2: int = 26, reps: int = 3):
+    """The step's calls by the parallel float32 CPU baseline (std::thread over
+    the cores of this process's affinity mask) on n = 2^sample_log2 elements
+    per call (grids 2^(k/2) square, rowdot rows of 2^(k/2), the batched
+    instances of the workload with lengths scaled by the same factor), each
+    call the median of `reps` runs; GB/s of the same algorithmic bytes as the
+    GPU step."""
+    import cpu_baseline as cb
+    n = 1 << sample_log2
+    side = 1 << (sample_log2 // 2)
+    x, y = syn.uniform_f32(syn.SEED_X, n), syn.uniform_f32(syn.SEED_Y, n)
+    xi = syn.uniform_int(syn.SEED_INT, n, 0, 100)
+    g = syn.uniform_f32(syn.SEED_GRID, n, 0.0, 1.0).reshape(side, side)
+    M = syn.uniform_f32(syn.SEED_MAT, n).reshape(n // side, side)
+    A = syn.uniform_f32(syn.SEED_X + 7, side)
+    Ag = syn.uniform_f32(syn.SEED_X + 8, GATHER_M)
+    idx = syn.uniform_int(syn.SEED_IDX, n, 0, GATHER_M - 1)
+    scale = n / N
+    lens = np.maximum(1, (syn.loguniform_lengths(syn.SEED_BATCH_LEN, BATCH_B) * scale).astype(np.int64))
+    off = syn.csr_offsets(lens)
+    bv = syn.uniform_f32(syn.SEED_BATCH_VAL, int(off[-1]))
+    w9 = np.outer([1, 2, 1], [1, 2, 1]).astype(np.float32) / np.float32(16)
+    w5 = np.array([[0, 1, 0], [1, 4, 1], [0, 1, 0]], np.float32) / np.float32(8)
+    w1 = (np.array([math.comb(2 * R1D, k) for k in range(2 * R1D + 1)], np.float64) / 4 ** R1D).astype(np.float32)
+    oA, oB, oI = np.empty_like(x), np.empty_like(x), np.empty_like(xi)
+    oG, rd = np.empty_like(g), np.empty(n // side, np.float32)
+    bres, bsc = np.empty(BATCH_B, np.float32), np.empty_like(bv)
+    tb = int(off[-1])
+    calls = [
+        ("map_axpy", 12 * n, lambda: cb.map_axpy(x, y, 2.5, oA)),
+        ("reduce_sum", 4 * n, lambda: cb.reduce_sum(x)),
+        ("reduce_max", 4 * n, lambda: cb.reduce_max(x)),
+        ("mapreduce_dot", 8 * n, lambda: cb.dot(x, y)),
+        ("scan_incl_i32", 8 * n, lambda: cb.scan_i32(xi, True, oI)),
+        ("scan_excl_f32", 8 * n, lambda: cb.scan_f32(x, False, oB)),
+        ("mapoverlap2d_9pt", 8 * n, lambda: cb.stencil2d(g, w9, oG)),
+        ("mapoverlap2d_5pt", 8 * n, lambda: cb.stencil2d(g, w5, oG)),
+        ("mapoverlap1d_r8", 8 * n, lambda: cb.stencil1d(x, R1D, w1, oA)),
+        ("maparray_rowdot", 4 * n + 4 * side + 4 * (n // side), lambda: cb.rowdot(A, M, rd)),
+        ("maparray_gather", 8 * n, lambda: cb.gather(Ag, idx, oB)),
+        ("batched_sumsq_scan", 8 * tb + 8 * (BATCH_B + 1) + 4 * BATCH_B, lambda: cb.batched(bv, off, bres, bsc)),
+        ("map_tanh_bwd", 12 * n, lambda: cb.map_tanh_bwd(x, y, oA)),
+        ("scan_bwd_f32", 8 * n, lambda: cb.scan_bwd_f32(x, oB)),
+        ("mapoverlap2d_9pt_bwd", 8 * n, lambda: cb.stencil2d_bwd(g, w9, oG)),
+    ]
+    per, tot_t, tot_b = {}, 0.0, 0
+    for name, nb, fn in calls:
+        fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        per[name] = round(nb / t / 1e9, 2)
+        tot_t += t
+        tot_b += nb
+    host = cb.host_cpu()
+    return {"value": round(tot_b / tot_t / 1e9, 2), "unit": "GB/s", "cores": cb.cores(), "cpu_model": host["model"],
+            "kind": "parallel float32 CPU baseline (std::thread, cpu_baseline/cpu_parallel.cpp)",
+            "sample": f"every call of the step on n = 2^{sample_log2} elements (grids {side}^2), median of {reps} "
+                      f"runs per call, {tot_t:.2f} s per step", "per_call_GB/s": per}
+
+
+def host_model() -> str:
+    import cpu_baseline as cb
+    return cb.host_cpu()["model"]
 
 
 def run_reference(args):
@@ -310,6 +394,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(),
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "cpu_model": host_model(),
                              "sample": f"each step: every skeleton of the step on n = {sample} elements "
                                        "(float64 oracle, one thread)"},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -497,6 +582,155 @@ def _event_ms(torch, stream, fn, reps, lead_ns=0):
     return statistics.median(ts)
 
 
+def launch_floor(sk, torch, stream, count: int = 200) -> float:
+    """Microseconds per launch of an empty kernel, launched back to back
+    (after a sleep kernel that covers the host's enqueue time)."""
+    sk.skel_probe_empty_launches(16)
+    ms = _event_ms(torch, stream, lambda: sk.skel_probe_empty_launches(count), 5, lead_ns=2_000_000)
+    return ms * 1e3 / count
+
+
+def l2_random_rate(sk, torch, stream, m: int = 1 << 20, reads: int = 1 << 28):
+    """Random 4-byte reads per second from an L2-resident table of m floats
+    (the gather's table size): the gather's measured ceiling."""
+    dev = torch.device("cuda")
+    table = torch.from_numpy(syn.uniform_f32(syn.SEED_X + 8, m)).to(dev)
+    sink = torch.zeros(1, device=dev)
+    made = sk.skel_probe_l2_random(table, reads, sink)
+    ms = _event_ms(torch, stream, lambda: sk.skel_probe_l2_random(table, reads, sink), 5)
+    return made / (ms * 1e-3), ms
+
+
+def chains_leg(sk, torch, stream, steps: int = 10, reps: int = 3):
+    """Ten chained 2D MapOverlap calls (5- and 9-point, clamp) on square grids
+    of side 512, 2048, 8192 and 16384 from an input valid only in pinned host
+    memory: the composed chain (variant and steps per pass from the table)
+    against ten single calls; device time of the chain on device-resident
+    data, and host-timed end to end (input marked host-valid, chain, result
+    read on the host) with and without the final device-to-host read;
+    transfers counted over one end-to-end run."""
+    res = {}
+    for side in (512, 2048, 8192, 16384):
+        x = torch.from_numpy(syn.uniform_f32(syn.SEED_GRID, side * side, 0.0, 1.0).reshape(side, side)).pin_memory()
+        cin = sk.Container.from_host(x.numpy())
+        a, b = sk.Container.empty((side, side)), sk.Container.empty((side, side))
+        for kind in ("stencil5", "stencil9"):
+            forms = {"composed": lambda: sk.skel_mapoverlap_chain(kind, None, "clamp", steps, cin, b, a)}
+
+            def single():
+                src = cin
+                for k in range(steps):
+                    dst = a if k % 2 == 0 else b
+                    sk.skel_mapoverlap(kind, 1, None, "clamp", src, dst)
+                    src = dst
+            forms["single_calls"] = single
+            for fname, fn in forms.items():
+                outc = a if fname == "composed" or steps % 2 == 1 else b
+
+                def e2e(read_back):
+                    cin.mark(sk.UNIT_HOST)
+                    fn()
+                    if read_back:
+                        outc.host_ptr(sk.READ, stream)
+                    else:
+                        torch.cuda.synchronize()
+                e2e(True)
+                s0 = (cin.stats(), outc.stats())
+                e2e(True)
+                s1 = (cin.stats(), outc.stats())
+                fn()                                      # input now device-valid: device time only
+                ms_dev = _event_ms(torch, stream, fn, reps, lead_ns=1_000_000)
+                variant = list(sk.skel_last_variant("chain2d")) if fname == "composed" else None
+                t_in, t_all = [], []
+                for _ in range(reps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    e2e(False)
+                    t_in.append(time.perf_counter() - t0)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    e2e(True)
+                    t_all.append(time.perf_counter() - t0)
+                key = f"{kind[7:]}pt_{side}sq"
+                res.setdefault(key, {})[fname] = {
+                    "ms_device": round(ms_dev, 3),
+                    "GB/s_per_call": round(8 * side * side * steps / (ms_dev * 1e-3) / 1e9, 1),
+                    "ms_e2e_excl_d2h": round(1e3 * statistics.median(t_in), 3),
+                    "ms_e2e_incl_d2h": round(1e3 * statistics.median(t_all), 3),
+                    "transfers_h2d_d2h": [s1[0]["h2d"] - s0[0]["h2d"], s1[1]["d2h"] - s0[1]["d2h"]],
+                    **({"variant": variant} if variant else {})}
+            r = res[f"{kind[7:]}pt_{side}sq"]
+            r["speedup_composed"] = round(r["single_calls"]["ms_device"] / r["composed"]["ms_device"], 3)
+        for c in (cin, a, b):
+            c.close()
+        del x
+    return res
+
+
+# per-kernel algorithmic bytes per grid point of the composed loss's calls
+AUTOGRAD_BYTES = {"fwd_map_tanh": 8, "fwd_mapoverlap_9pt": 8, "fwd_sumsq_stencil": 4, "fwd_row_scan": 8,
+                  "fwd_sumsq_scan": 4, "fwd_combine": 0, "bwd_scale": 0, "bwd_sumsq_stencil": 8,
+                  "bwd_mapoverlap_9pt": 8, "bwd_sumsq_scan": 8, "bwd_reverse_scan": 8, "bwd_add": 12,
+                  "bwd_map_tanh": 12}
+
+
+def autograd_per_kernel(torch, stream, xg, reps: int = 5):
+    """Device time and GB/s of every skeleton call of the composed loss's
+    forward and backward (events around each call; a sleep kernel ahead of
+    each pass keeps the host's enqueue time out of the intervals)."""
+    from paper_1405_2915_gb300.autograd import composed_loss
+    pts = xg.numel()
+    acc = {}
+    for _ in range(reps):
+        evs = []
+
+        def step(name, fn):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(torch.cuda.current_stream())
+            fn()
+            e1.record(torch.cuda.current_stream())
+            evs.append((name, e0, e1))
+        xg.grad = None
+        torch.cuda._sleep(40_000_000)
+        composed_loss(xg, step=step).backward()
+        torch.cuda.synchronize()
+        for name, e0, e1 in evs:
+            acc.setdefault(name, []).append(e0.elapsed_time(e1))
+    res = {}
+    for name, ts in acc.items():
+        ms = statistics.median(ts)
+        nb = AUTOGRAD_BYTES.get(name, 0) * pts
+        res[name] = {"ms": round(ms, 4), **({"GB/s": round(nb / (ms * 1e-3) / 1e9, 1)} if nb else {})}
+    return res
+
+
+def overhead_leg(sk, torch, stream, per_sk):
+    """Host cost of a skeleton call (argument checks, table lookup, coherence
+    steps of three containers, launch) against a bare launch of the same
+    kernel, measured inside the library; as a fraction of the kernel's device
+    time for axpy at 2^20, 2^24 and 2^28 elements (Sec. IV: container
+    overhead)."""
+    us_call, us_launch = sk.skel_probe_call_overhead(200, 1024)
+    over = us_call - us_launch
+    dev = torch.device("cuda")
+    kern = {}
+    for k in (20, 24):
+        n = 1 << k
+        x, y, o = (torch.empty(n, device=dev).uniform_() for _ in range(3))
+        cx, cy, co = (sk.Container.from_tensor(t) for t in (x, y, o))
+        fn = lambda: sk.skel_map("axpy", [cx, cy], co, [2.5])
+        fn()
+        kern[f"2^{k}"] = _event_ms(torch, stream, fn, 5, lead_ns=500_000) * 1e3
+        for c in (cx, cy, co):
+            c.close()
+    if "map_axpy" in per_sk:
+        kern["2^28"] = per_sk["map_axpy"]["ms"] * 1e3
+    return {"us_per_call": round(us_call, 3), "us_per_bare_launch": round(us_launch, 3),
+            "overhead_us": round(over, 3),
+            "overhead_frac_of_axpy_kernel": {k: round(over / v, 5) for k, v in kern.items()},
+            "axpy_kernel_us": {k: round(v, 2) for k, v in kern.items()}}
+
+
 def config_legs(sk, torch, stream):
     """Measurements of the other workload configurations, reported apart
     from the step: dot at n = 2^20 (latency-bound, cold and warm L2), a
@@ -531,33 +765,26 @@ def config_legs(sk, torch, stream):
     for _ in range(10):
         flush.sum()                                   # evict the operands from L2
         cold.append(_event_ms(torch, stream, dot, 1))
+    # error against the exact sum: float32 products are exact in float64 and
+    # math.fsum rounds the exact sum once
+    xh, yh = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+    prods = xh * yh
+    exact, abs_sum = math.fsum(prods.tolist()), math.fsum(np.abs(prods).tolist())
+    got = float(sk.skel_mapreduce("mul", "add", [cx, cy]))
+    l0 = sk.lib.skel_launch_count()
+    dot()
+    launches = sk.lib.skel_launch_count() - l0
+    floor = launch_floor(sk, torch, stream)
     out["dot_2e20"] = {"us_warm": round(warm * 1e3, 2), "us_cold": round(statistics.median(cold) * 1e3, 2),
                        "GB/s_warm": round(8 * n / (warm * 1e-3) / 1e9, 1),
-                       "GB/s_cold": round(8 * n / (statistics.median(cold) * 1e-3) / 1e9, 1)}
+                       "GB/s_cold": round(8 * n / (statistics.median(cold) * 1e-3) / 1e9, 1),
+                       "error_ratio": round(abs(got - exact) / (2.0 ** -20 * abs_sum), 4),
+                       "error_ratio_def": "|gpu - exact| / (2^-20 * sum |x_i y_i|), exact = math.fsum of the float64 products",
+                       "launches_per_call": launches, "variant": list(sk.skel_last_variant("mapreduce")),
+                       "launch_floor_us": round(launches * floor, 2),
+                       "launch_floor_def": f"{launches} back-to-back launches of an empty kernel ({floor:.2f} us each)"}
     del flush
-    # 10-step 9-point chain, 8192^2
-    side, steps = 8192, 10
-    g = torch.from_numpy(syn.uniform_f32(syn.SEED_GRID, side * side, 0.0, 1.0).reshape(side, side)).to(dev)
-    o, t = torch.empty_like(g), torch.empty_like(g)
-    cg, co, ct = (sk.Container.from_tensor(v) for v in (g, o, t))
-    chain = lambda: sk.skel_mapoverlap_chain("stencil9", None, "clamp", steps, cg, ct, co)
-    chain()
-    ms_chain = _event_ms(torch, stream, chain, 5)
-    variant = list(sk.skel_last_variant("chain2d"))
-
-    def per_call():
-        src = cg
-        for k in range(steps):
-            dst = co if (steps - 1 - k) % 2 == 0 else ct
-            sk.skel_mapoverlap("stencil9", 1, None, "clamp", src, dst)
-            src = dst
-    per_call()
-    ms_calls = _event_ms(torch, stream, per_call, 5)
-    out["chain_9pt_8192sq_x10"] = {"ms_composed": round(ms_chain, 3), "ms_per_call": round(ms_calls, 3),
-                                   "speedup": round(ms_calls / ms_chain, 3), "variant": variant,
-                                   "GB/s_equivalent": round(8 * side * side * steps / (ms_chain * 1e-3) / 1e9, 1)}
-    for c in (cg, co, ct):
-        c.close()
+    out["chains_10x"] = chains_leg(sk, torch, stream)
     # batched: graph replay against per-instance calls
     lens = syn.loguniform_lengths(syn.SEED_BATCH_LEN, BATCH_B)
     off = syn.csr_offsets(lens)
@@ -578,8 +805,16 @@ def config_legs(sk, torch, stream):
             sk.skel_scan("add", True, v, sv)
     separate()
     ms_sep = _event_ms(torch, stream, separate, 2)
+    fused_b = 8 * total + 8 * (BATCH_B + 1) + 4 * BATCH_B
+    two_pass_b = 12 * total + 8 * (BATCH_B + 1) + 4 * BATCH_B
     out["batched_4096"] = {"ms_graph": round(ms_graph, 3), "ms_separate_calls": round(ms_sep, 3),
-                           "speedup": round(ms_sep / ms_graph, 2), "calls_separate": 2 * len(views)}
+                           "speedup": round(ms_sep / ms_graph, 2), "calls_separate": 2 * len(views),
+                           "elements": total,
+                           "GB/s_fused_bytes": round(fused_b / (ms_graph * 1e-3) / 1e9, 1),
+                           "GB/s_two_pass_bytes": round(two_pass_b / (ms_graph * 1e-3) / 1e9, 1),
+                           "bytes_def": "fused: 8 B/elem (read + write once) + offsets and results; "
+                                        "two passes: 12 B/elem (the sum of squares reads the values again)",
+                           "variant": list(sk.skel_last_variant("batched"))}
     for v, sv, rv in views:
         v.close(); sv.close(); rv.close()
     plan.close()
@@ -587,6 +822,7 @@ def config_legs(sk, torch, stream):
         c.close()
     # composed loss forward + backward, 8192^2
     from paper_1405_2915_gb300.autograd import composed_loss
+    side = 8192
     xg = torch.from_numpy(syn.uniform_f32(syn.SEED_GRAD, side * side).reshape(side, side)).to(dev)
     xg.requires_grad_(True)
 
@@ -594,8 +830,8 @@ def config_legs(sk, torch, stream):
         xg.grad = None
         composed_loss(xg).backward()
     fwd_bwd()
-    ms_ad = _event_ms(torch, stream, fwd_bwd, 5)
-    out["autograd_8192sq"] = {"ms_fwd_bwd": round(ms_ad, 3)}
+    ms_ad = _event_ms(torch, stream, fwd_bwd, 5, lead_ns=20_000_000)
+    out["autograd_8192sq"] = {"ms_fwd_bwd": round(ms_ad, 3), "per_kernel": autograd_per_kernel(torch, stream, xg)}
     # the composed chain tanh -> 9-point stencil -> sum of squares, 8192^2,
     # per call (three dispatched calls) against fused (one pass)
     cxg = sk.Container.from_tensor(xg.detach())
@@ -709,7 +945,7 @@ def main():
         args.no_e2e = args.no_cpu = True
     if args.only:
         keep = set(args.only.split(","))
-        calls = [c for c in calls if c[0] in keep]
+        calls = [c for c in calls + wl.extra_calls() if c[0] in keep]
         if not calls:
             ap.error("--only matched no call")
         args.no_e2e = args.no_cpu = True
@@ -763,6 +999,23 @@ def main():
     roofline = {"bound": "hbm", "kernel": dom[0], "achieved": round(dom_gbs, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(dom_gbs / hbm, 3), "peak_kind": peak_kind,
                 "traffic": committed_traffic(dom[0])}
+    l2 = None
+    if not args.force:
+        rate, l2_ms = l2_random_rate(sk, torch, stream)
+        l2 = {"reads_per_s": round(rate / 1e9, 2), "unit": "1e9 reads/s", "ms": round(l2_ms, 4),
+              "what": "random 4-byte reads from a 4 MiB table (2^20 floats), one wave of 8 blocks per SM"}
+        if "maparray_gather" in per:
+            g_ms = per["maparray_gather"] / args.steps
+            g_rate = N / (g_ms * 1e-3)
+            l2["gather_frac"] = round(g_rate / rate, 3)
+            if dom[0] == "maparray_gather":
+                # the gather's table reads are random L2 sectors: its roofline is
+                # the measured random-read rate, in the gather's own units (8
+                # algorithmic bytes per read: the index read and the output write)
+                roofline = {"bound": "l2", "kernel": dom[0], "achieved": round(dom_gbs, 1),
+                            "peak": round(8 * rate / 1e9, 1), "unit": "GB/s", "frac": round(g_rate / rate, 3),
+                            "peak_kind": "measured (skel_probe_l2_random), 8 algorithmic bytes per random read",
+                            "hbm_peak": hbm, "hbm_frac": round(dom_gbs / hbm, 3), "traffic": committed_traffic(dom[0])}
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -770,12 +1023,18 @@ def main():
             "frac_of_peak": round(value / world / hbm, 3),
             "tuned_vs_default_speedup": round(def_ms / total_ms, 3), "dispatch_table": tuned,
             "per_skeleton": per_sk, "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
-            "input_gen_s": round(wl.gen_s, 1)}
+            "input_gen_s": round(wl.gen_s, 1), "l2_random_probe": l2}
+    try:
+        import cpu_baseline as cb
+        line["host"] = cb.host_cpu()
+    except Exception as e:  # the host description is informative only
+        line["host"] = {"error": str(e)}
     del wl, calls
     torch.cuda.empty_cache()
     if not args.only and not args.force and not args.no_next:
         line["next"] = {"coulomb_grid": coulomb_leg(sk, torch, stream, clocks)}
         line["configs"] = config_legs(sk, torch, stream)
+        line["configs"]["call_overhead"] = overhead_leg(sk, torch, stream, per_sk)
     if not args.no_e2e:
         dt, h2d, d2h, cpus, per_step = e2e_run(sk, torch, min(args.steps, 5), stream)
         dt = max_over_ranks(dt * 1e3) / 1e3
@@ -786,6 +1045,7 @@ def main():
                        "host_cpus": "gpu-local" if cpus else "unchanged"}
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
+        line["cpu_parallel"] = cpu_parallel_leg()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -498,6 +498,37 @@ int skel_check_device(void *stream);
  * microseconds (default 2,000,000). */
 int skel_set_debug(int key, int64_t value);
 
+/* ------------------------------------------------ measurement probes --- */
+
+/* Enqueues `count` launches of an empty kernel on `stream`, back to back.
+ * Timed with events around them, they give this GPU's launch floor: the
+ * least time a call made of k dependent launches can take (the bound of a
+ * small, latency-bound call such as the MapReduce dot product at n = 2^20).
+ * Returns without waiting. */
+int skel_probe_empty_launches(int count, void *stream);
+
+/* Enqueues about `reads` random 4-byte reads from `table` (device memory, m
+ * floats, m a power of two <= 2^31; it stays in L2 when m * 4 bytes is well
+ * below the L2's size) over one wave of blocks, with indices from a
+ * per-thread generator in registers and no output stream; `sink` (one
+ * device float) is never written in practice.  *reads_made receives the
+ * number of reads the launch makes (rounded up to whole batches).  Timed with
+ * events, reads_made / time is the random-sector rate that bounds MapArray's
+ * gather, whose reads of A have the same pattern.  Returns without waiting. */
+int skel_probe_l2_random(const float *table, int64_t m, int64_t reads, float *sink, int64_t *reads_made,
+                         void *stream);
+
+/* The host cost of a skeleton call against a bare launch of its kernel
+ * (Sec. IV: the smart containers' overhead).  Creates three float32
+ * containers of n elements (device-valid), then times on the host, with a
+ * steady clock, `calls` skel_map(AXPY) calls (argument checks, table lookup,
+ * the coherence steps of three operands, the launch) and `calls` launches of
+ * the same kernel variant with the same arguments and no container or table
+ * work.  *us_call and *us_launch receive microseconds per call.  Synchronises
+ * `stream`; destroys the containers.  With calls kept below the device's
+ * launch queue depth (a few hundred) neither loop waits for the GPU. */
+int skel_probe_call_overhead(int calls, int64_t n, double *us_call, double *us_launch, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -423,3 +423,24 @@ def skel_coherence_step(valid: int, unit: int, mode: int):
 
 def skel_version() -> str:
     return lib.skel_version().decode()
+
+
+# ------------------------------------------------------- measurement probes ---
+def skel_probe_empty_launches(count: int, stream=None) -> None:
+    check(lib.skel_probe_empty_launches(int(count), _stream(stream)))
+
+
+def skel_probe_l2_random(table, reads: int, sink, stream=None) -> int:
+    """table, sink: float32 CUDA tensors (table length a power of two).
+    Returns the number of reads the launch makes."""
+    made = C.c_int64()
+    check(lib.skel_probe_l2_random(C.c_void_p(table.data_ptr()), table.numel(), int(reads),
+                                   C.c_void_p(sink.data_ptr()), C.byref(made), _stream(stream)))
+    return made.value
+
+
+def skel_probe_call_overhead(calls: int, n: int, stream=None):
+    """(microseconds per skel_map call, microseconds per bare launch of its kernel)."""
+    a, b = C.c_double(), C.c_double()
+    check(lib.skel_probe_call_overhead(int(calls), int(n), C.byref(a), C.byref(b), _stream(stream)))
+    return a.value, b.value

@@ -74,6 +74,9 @@ SIGNATURES = {
     "skel_variant_name": (C.c_char_p, [i32, i32]),
     "skel_check_device": (i32, [vp]),
     "skel_set_debug": (i32, [i32, i64]),
+    "skel_probe_empty_launches": (i32, [i32, vp]),
+    "skel_probe_l2_random": (i32, [vp, i64, i64, vp, C.POINTER(i64), vp]),
+    "skel_probe_call_overhead": (i32, [i32, i64, C.POINTER(dbl), C.POINTER(dbl), vp]),
 }
 
 

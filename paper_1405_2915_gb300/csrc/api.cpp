@@ -3,6 +3,7 @@
 // its CUDA variants.  See include/skel.h for the contract of every function.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -1577,5 +1578,66 @@ int skel_check_device(void *stream)
 }
 
 int skel_set_debug(int key, int64_t value) { return guarded([&] { return set_debug(key, value); }); }
+
+// ------------------------------------------------------------- probes --
+
+int skel_probe_empty_launches(int count, void *stream)
+{
+    return guarded([&] {
+        if (count < 0) return fail(SKEL_ERR_INVALID_ARG, "probe: count must be >= 0");
+        return probe_launch_empty(count, (cudaStream_t)stream);
+    });
+}
+
+int skel_probe_l2_random(const float *table, int64_t m, int64_t reads, float *sink, int64_t *reads_made, void *stream)
+{
+    return guarded([&] {
+        if (!table || !sink || !reads_made) return fail(SKEL_ERR_INVALID_ARG, "probe: NULL pointer");
+        if (reads < 1) return fail(SKEL_ERR_INVALID_ARG, "probe: reads must be >= 1");
+        int rc = probe_launch_l2_random(table, m, reads, sink, (cudaStream_t)stream);
+        if (rc == SKEL_OK) *reads_made = probe_l2_random_reads(reads);
+        return rc;
+    });
+}
+
+int skel_probe_call_overhead(int calls, int64_t n, double *us_call, double *us_launch, void *stream)
+{
+    return guarded([&] {
+        if (calls < 1 || n < 1 || !us_call || !us_launch) return fail(SKEL_ERR_INVALID_ARG, "probe: bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t shape[1] = {n};
+        skel_handle x = nullptr, y = nullptr, o = nullptr;
+        int rc = skel_container_create(SKEL_F32, 1, shape, &x);
+        if (!rc) rc = skel_container_create(SKEL_F32, 1, shape, &y);
+        if (!rc) rc = skel_container_create(SKEL_F32, 1, shape, &o);
+        const double a = 2.5;
+        const skel_handle ins[2] = {x, y};
+        void *px = nullptr, *py = nullptr, *po = nullptr;
+        if (!rc) rc = skel_container_device_ptr(x, SKEL_WRITE, stream, &px);     // device-valid operands
+        if (!rc) rc = skel_container_device_ptr(y, SKEL_WRITE, stream, &py);
+        if (!rc) rc = skel_container_device_ptr(o, SKEL_WRITE, stream, &po);
+        for (int k = 0; k < 10 && !rc; ++k) rc = skel_map(SKEL_FN_AXPY, &a, 1, ins, 2, o, stream);
+        if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "probe sync");
+        // the whole call: argument checks, table lookup, coherence steps, launch
+        auto t0 = std::chrono::steady_clock::now();
+        for (int k = 0; k < calls && !rc; ++k) rc = skel_map(SKEL_FN_AXPY, &a, 1, ins, 2, o, stream);
+        auto t1 = std::chrono::steady_clock::now();
+        if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "probe sync");
+        // the same kernel launched directly with the choice the call made
+        Choice c{};
+        if (!rc) rc = last_choice(SKEL_SK_MAP, &c);
+        MapLaunch m{SKEL_FN_AXPY, (float)a, (const float *)px, (const float *)py, (float *)po, n};
+        auto t2 = std::chrono::steady_clock::now();
+        for (int k = 0; k < calls && !rc; ++k) rc = launch_map(m, c, s);
+        auto t3 = std::chrono::steady_clock::now();
+        if (!rc) rc = cudaStreamSynchronize(s) == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "probe sync");
+        for (skel_handle h : {x, y, o})
+            if (h) skel_container_destroy(h);
+        if (rc) return rc;
+        *us_call = std::chrono::duration<double, std::micro>(t1 - t0).count() / calls;
+        *us_launch = std::chrono::duration<double, std::micro>(t3 - t2).count() / calls;
+        return (int)SKEL_OK;
+    });
+}
 
 }  // extern "C"

@@ -285,4 +285,11 @@ struct MapBwdLaunch {
 };
 int launch_map_bwd(const MapBwdLaunch &m, cudaStream_t s);
 
+// Measurement probes (k_probe.cu): empty launches back to back, and random
+// 4-byte reads from an L2-resident table of m (a power of two) floats; the
+// number of reads the latter makes for a request is probe_l2_random_reads.
+int probe_launch_empty(int count, cudaStream_t s);
+int probe_launch_l2_random(const float *table, int64_t m, int64_t reads, float *sink, cudaStream_t s);
+int64_t probe_l2_random_reads(int64_t reads);
+
 }  // namespace skel
