@@ -27,6 +27,13 @@
 //                       the aggregate before the in-place scans (16-byte
 //                       aligned operands; reverse and row-wise scans need
 //                       segments of a multiple of 4 elements).
+//   7 lookback_hybrid   one block per tile staged partly in shared memory
+//                       by bulk copies, partly in registers (tile=0: 96 + 64
+//                       KiB, 3: 96 + 80 KiB, two blocks per SM; 1: 64 + 32
+//                       KiB and 2: 64 + 48 KiB, three blocks per SM); warp
+//                       totals first, the aggregate published at once, the
+//                       look-back, then each warp scans and stores from its
+//                       offset (same operand rules as variant 5).
 //   6 lookback_ws       one persistent block per SM split into producer,
 //                       scanner, look-back and store warps that pass tiles
 //                       through a ring of staged tiles (tile=0: four 48 KiB
@@ -509,6 +516,260 @@ scan_big(const T *__restrict__ in, T *__restrict__ out, SegGeom g, LookbackDesc 
         ms.len = len - off < kTmaTile ? len - off : kTmaTile;
         ms.vec = ms.len == kTmaTile;
         dev::tile_store<T, kBlock, kTmaV>(out, ms, v);
+    }
+}
+
+// ------------------------------------ variant 7: hybrid-staged tiles --
+// One block per tile of (SUBS + SUBR) x 4096 elements, drawn in ticket
+// order: the first SUBS sub-tiles arrive by bulk copies into shared memory,
+// the last SUBR by 16-byte loads into registers (16 elements per thread
+// each).  A tile waits in its look-back until every earlier tile's
+// aggregate is out, in practice for the slowest load among the few hundred
+// tiles in flight, so the scan's rate is set by how many bytes the SMs hold
+// while their tiles wait; the registers add to what shared memory holds
+// (three blocks of 64 KiB + 48 KiB hold 336 KiB per SM, against 192 KiB for
+// four blocks of 48 KiB staged in shared memory alone).
+//   pass 1: each warp sums its 512 elements of every sub-tile; one warp
+//           scans those totals, which gives every warp its offset in the
+//           tile and the tile aggregate, published at once;
+//   look-back over the predecessors (all warps, a window of 32 each);
+//   pass 2: each warp scans its elements with shuffles from its offset plus
+//           the tile prefix and stores them (no shared-memory writes).
+// Forward and reverse, 1D and per row (a reverse or row-wise scan needs
+// segments of a multiple of 4 elements, like variant 5).  PART = false: the
+// whole tiles, drawn in ticket order (tile = s * tps + ti, ti < tpsf); PART =
+// true: a second launch, after the first on the same stream, for the last,
+// partial tile of every segment (block s), whose predecessors are all out by
+// then.  Keeping the ragged-tile logic out of the first kernel keeps its
+// loops free of bounds checks and its registers below the three-blocks-per-
+// SM limit.
+template <class T, bool INCL, bool REV, int SUBS, int SUBR, int MINB, bool PART>
+__global__ void __launch_bounds__(kBlock, MINB)
+scan_hybrid(const T *__restrict__ in, T *__restrict__ out, SegGeom g, int64_t tpsf, LookbackDesc d, Control *ctl,
+            uint32_t epoch, int64_t skip_tile, uint64_t limit_ns)
+{
+    using CT = typename ScanTypes<T>::CT;
+    using V4 = typename ScanTypes<T>::V4;
+    using AddOp = typename std::conditional<std::is_same<T, float>::value, dev::AddF, dev::AddU>::type;
+    constexpr int NW = kBlock / 32, NS = SUBS + SUBR, TILE = NS * kTmaTile, SLEN = SUBS * kTmaTile;
+    static_assert(NS * NW <= 96, "one warp scans at most 96 warp totals");
+    extern __shared__ __align__(1024) unsigned char dyn[];   // SUBS * 16 KiB
+    const T *buf = reinterpret_cast<const T *>(dyn);
+    __shared__ __align__(8) uint64_t bars[SUBS];
+    __shared__ int64_t s_tile;
+    __shared__ T wtot[NS * NW], wex[NS * NW];
+    __shared__ T s_agg;
+    __shared__ dev::WideLookbackSmem<CT, NW> lbs;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // tile -> (segment, index in it) and its placement
+    auto place = [&](int64_t t, int64_t &seg, int64_t &ti, int64_t &base, int &len) {
+        if (PART) { seg = t; ti = tpsf; }
+        else { seg = t / tpsf; ti = t - seg * tpsf; }
+        const int64_t e0 = ti * TILE, seg0 = seg * g.seglen;
+        len = PART ? (int)(g.seglen - e0) : TILE;
+        base = REV ? seg0 + g.seglen - 1 - e0 : seg0 + e0;
+    };
+    if (threadIdx.x == 0) {
+        int64_t t;
+        if (PART) t = blockIdx.x;
+        else {
+            t = atomicAdd(&ctl->ticket, 1u);
+            if (t == (int64_t)gridDim.x - 1) ctl->ticket = 0u;   // the last ticket: every block has drawn
+        }
+        s_tile = t;
+#pragma unroll
+        for (int c = 0; c < SUBS; ++c) mbar_init(&bars[c]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        int64_t seg0, ti0, base0;
+        int len0;
+        place(t, seg0, ti0, base0, len0);
+        const int slen0 = len0 < SLEN ? len0 : SLEN;
+        // staged physical range: [base, base + slen) forward, [base - slen + 1, base] reverse
+        const int64_t pstart = REV ? base0 - (slen0 - 1) : base0;
+        const uint32_t bytes = (uint32_t)(slen0 * (int)sizeof(T)) & ~15u;
+#pragma unroll
+        for (int c = 0; c < SUBS; ++c) {
+            const uint32_t b = smem_u32(&bars[c]), o = (uint32_t)c * 16384u;
+            if (o >= bytes) {   // nothing staged in this chunk: complete its phase at once
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
+                continue;
+            }
+            const uint32_t sz = bytes - o < 16384u ? bytes - o : 16384u;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(sz) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(smem_u32(dyn + o)), "l"(reinterpret_cast<const unsigned char *>(in + pstart) + o),
+                            "r"(sz), "r"(b)
+                         : "memory");
+        }
+    }
+    __syncthreads();
+    int64_t segi, ti, mbase;
+    int len;
+    place(s_tile, segi, ti, mbase, len);
+    const int64_t first = segi * g.tps, tile = first + ti;
+    // offsets inside the tile fit in 32 bits; the operands are 16-byte
+    // aligned and tiles start on multiples of 4 elements, so every group of
+    // four that lies inside the tile is one aligned 16-byte access
+    const int slen = len < SLEN ? len : SLEN;
+    const int whole = slen & ~3;   // staged elements (reverse: slen % 4 == 0, all staged)
+    const T *src = in + mbase;     // logical e at src[e] forward, src[-e] reverse
+    T *dst = out + mbase;
+    auto load4 = [&](const T *p0, int e) -> V4 {   // logical e..e+3 from global memory
+        V4 q;
+        if (!PART || e + 3 < len) {
+            if (!REV) q = dev::ld_stream(reinterpret_cast<const V4 *>(p0 + e));
+            else {
+                const V4 r4 = dev::ld_stream(reinterpret_cast<const V4 *>(p0 - e - 3));
+                q.x = r4.w; q.y = r4.z; q.z = r4.y; q.w = r4.x;
+            }
+        } else {   // the last, partial group of a forward 1D scan
+            q.x = e < len ? p0[e] : T(0);
+            q.y = e + 1 < len ? p0[e + 1] : T(0);
+            q.z = e + 2 < len ? p0[e + 2] : T(0);
+            q.w = T(0);
+        }
+        return q;
+    };
+    // the register sub-tiles: logical elements SLEN + r * 4096 + w * 512 + k * 128 + lane * 4 + i
+    V4 rv[SUBR][4];
+#pragma unroll
+    for (int r = 0; r < SUBR; ++r)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) rv[r][k] = load4(src, SLEN + r * kTmaTile + w * 512 + k * 128 + lane * 4);
+    // input values of logical e..e+3 of the shared-memory part
+    auto src4 = [&](int e) -> V4 {
+        if (!PART || e + 3 < whole) {
+            if (!REV) return *reinterpret_cast<const V4 *>(buf + e);
+            const V4 r4 = *reinterpret_cast<const V4 *>(buf + (slen - 4 - e));
+            V4 q;
+            q.x = r4.w; q.y = r4.z; q.z = r4.y; q.w = r4.x;
+            return q;
+        }
+        if (e >= slen) return V4{T(0), T(0), T(0), T(0)};
+        return load4(src, e);   // the unstaged forward tail (fewer than 4 elements) is read directly
+    };
+    // Bounded wait for chunk c; block-uniform.  On failure the block records
+    // the timeout, waits (bounded) for every copy still landing in its
+    // shared memory and leaves; its tile is never published, so its
+    // successors' bounded waits give up too.
+    auto wait_chunk = [&](int c) -> bool {
+        uint32_t done = 0;
+        for (uint32_t k = 0; k < (1u << 22) && !done; ++k) done = mbar_try(&bars[c], 0);
+        if (__syncthreads_and(done)) return true;
+        if (threadIdx.x == 0) atomicOr(&ctl->error, kErrTimeout);
+        for (int cc = 0; cc < SUBS; ++cc) {
+            uint32_t dd = 0;
+            for (uint32_t k = 0; k < (1u << 22) && !dd; ++k) dd = mbar_try(&bars[cc], 0);
+        }
+        return false;
+    };
+    // pass 1: warp totals of every sub-tile.  Forward, logical sub-tile j is
+    // staged chunk j, so it starts as soon as that chunk has landed; reverse,
+    // the logical order runs backwards through the staged range, so every
+    // chunk is awaited first.
+    if (REV) {
+#pragma unroll
+        for (int j = 0; j < SUBS; ++j)
+            if (!wait_chunk(j)) return;
+    }
+#pragma unroll
+    for (int j = 0; j < SUBS; ++j) {
+        if (!REV && !wait_chunk(j)) return;
+        T gs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const V4 q = src4(j * kTmaTile + w * 512 + k * 128 + lane * 4);
+            gs[k] = (q.x + q.y) + (q.z + q.w);
+        }
+        const T s = dev::warp_reduce<AddOp>((gs[0] + gs[1]) + (gs[2] + gs[3]));
+        if (lane == 0) wtot[j * NW + w] = s;
+    }
+#pragma unroll
+    for (int r = 0; r < SUBR; ++r) {
+        T gs[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gs[k] = (rv[r][k].x + rv[r][k].y) + (rv[r][k].z + rv[r][k].w);
+        const T s = dev::warp_reduce<AddOp>((gs[0] + gs[1]) + (gs[2] + gs[3]));
+        if (lane == 0) wtot[(SUBS + r) * NW + w] = s;
+    }
+    __syncthreads();
+    if (w == 0) {   // exclusive scan of the warp totals in tile order, PL per lane
+        constexpr int PL = (NS * NW + 31) / 32;
+        T a[PL];
+        T sum = T(0);
+#pragma unroll
+        for (int i = 0; i < PL; ++i) {
+            a[i] = PL * lane + i < NS * NW ? wtot[PL * lane + i] : T(0);
+            sum = sum + a[i];
+        }
+        const T inc = dev::warp_incl_scan_add(sum);
+        T ex = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) ex = T(0);
+#pragma unroll
+        for (int i = 0; i < PL; ++i) {
+            if (PL * lane + i < NS * NW) wex[PL * lane + i] = ex;
+            ex = ex + a[i];
+        }
+        if (lane == 31) s_agg = inc;
+    }
+    __syncthreads();
+    {
+        const T agg = s_agg;
+        const bool pub = tile != skip_tile;
+        if (pub && threadIdx.x == 0) {
+            constexpr int W = dev::Codec<CT>::W;
+            if (tile == first) dev::Codec<CT>::put(d.incl + tile * W, (CT)agg, epoch);
+            else dev::Codec<CT>::put(d.agg + tile * W, (CT)agg, epoch);
+        }
+        const CT p = dev::wide_lookback<CT, NW>(tile, first, (CT)agg, d, epoch, ctl, limit_ns, false,
+                                                pub && tile != first, lbs);
+        // this warp's base of every sub-tile: the tile prefix plus its offset
+        if (lane < NS) wtot[lane * NW + w] = dev::to_elem<T>(p + (CT)wex[lane * NW + w]);
+        __syncwarp();
+    }
+    // pass 2: scan each warp's elements from its base and store them
+    auto scan_store = [&](int j, const V4 (&v)[4]) {
+        const T base = wtot[j * NW + w];
+        T carry = T(0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = j * kTmaTile + w * 512 + k * 128 + lane * 4;
+            const T s0 = v[k].x, s1 = s0 + v[k].y, s2 = s1 + v[k].z, s3 = s2 + v[k].w;
+            const T wi = dev::warp_incl_scan_add(s3);
+            T lex = __shfl_up_sync(0xffffffffu, wi, 1);
+            if (lane == 0) lex = T(0);
+            const T wt = __shfl_sync(0xffffffffu, wi, 31);
+            const T b = base + (carry + lex);
+            V4 o;
+            if (INCL) { o.x = b + s0; o.y = b + s1; o.z = b + s2; o.w = b + s3; }
+            else { o.x = b; o.y = b + s0; o.z = b + s1; o.w = b + s2; }
+            if (!PART || e + 3 < len) {
+                if (!REV) dev::st_stream(reinterpret_cast<V4 *>(dst + e), o);
+                else {
+                    V4 r4;
+                    r4.x = o.w; r4.y = o.z; r4.z = o.y; r4.w = o.x;
+                    dev::st_stream(reinterpret_cast<V4 *>(dst - e - 3), r4);
+                }
+            } else {   // the last, partial group of a forward 1D scan
+                if (e < len) dst[e] = o.x;
+                if (e + 1 < len) dst[e + 1] = o.y;
+                if (e + 2 < len) dst[e + 2] = o.z;
+            }
+            carry = carry + wt;
+        }
+    };
+#pragma unroll
+    for (int j = 0; j < SUBS; ++j) {
+        if (PART && j * kTmaTile >= len) break;   // block-uniform
+        V4 v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = src4(j * kTmaTile + w * 512 + k * 128 + lane * 4);
+        scan_store(j, v);
+    }
+#pragma unroll
+    for (int r = 0; r < SUBR; ++r) {
+        if (PART && SLEN + r * kTmaTile >= len) break;   // block-uniform
+        scan_store(SUBS + r, rv[r]);
     }
 }
 
@@ -1215,11 +1476,72 @@ int run_scan_big(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
     return sub3 ? launch_scan_big<T, INCL, false, 3>(sc, early, s) : launch_scan_big<T, INCL, false, 4>(sc, early, s);
 }
 
+template <class T, bool INCL, bool REV, int SUBS, int SUBR, int MINB>
+int launch_scan_hybrid(const ScanLaunch &sc, cudaStream_t s)
+{
+    const T *in = static_cast<const T *>(sc.in);
+    T *out = static_cast<T *>(sc.out);
+    constexpr int TILE = (SUBS + SUBR) * kTmaTile;
+    SegGeom g;
+    g.seglen = sc.seg > 0 ? sc.seg : sc.n;
+    g.tps = ceil_div(g.seglen, TILE);
+    g.ntiles = g.tps * (sc.n / g.seglen);
+    g.rev = REV;
+    g.vec_ok = true;
+    const int64_t nseg = sc.n / g.seglen, tpsf = g.seglen / TILE, nfull = nseg * tpsf;
+    if (g.ntiles > 0x7fffffffLL || nseg > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
+    auto kfull = scan_hybrid<T, INCL, REV, SUBS, SUBR, MINB, false>;
+    auto kpart = scan_hybrid<T, INCL, REV, SUBS, SUBR, MINB, true>;
+    const int dyn = SUBS * kTmaTile * (int)sizeof(T);
+    cudaError_t ea = cudaFuncSetAttribute(kfull, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (ea == cudaSuccess) ea = cudaFuncSetAttribute(kpart, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (ea != cudaSuccess) return fail_cuda(ea, "scan hybrid: shared memory opt-in");
+    Scratch scr{};
+    int rc = get_scratch(s, 0, 2 * (size_t)g.ntiles, &scr);
+    if (rc) return rc;
+    LookbackDesc d{scr.words, scr.words + g.ntiles};
+    const DebugKnobs k = debug_knobs();
+    if (nfull > 0)
+        launch_kernel(kfull, (unsigned)nfull, kBlock, (size_t)dyn, s, in, out, g, tpsf, d, scr.ctl, scr.epoch,
+                      k.scan_skip_publish_tile, k.wait_limit_ns);
+    if (g.seglen % TILE)   // every segment's last, partial tile, after the whole ones
+        launch_kernel(kpart, (unsigned)nseg, kBlock, (size_t)dyn, s, in, out, g, tpsf, d, scr.ctl, scr.epoch,
+                      k.scan_skip_publish_tile, k.wait_limit_ns);
+    cudaError_t e = cudaPeekAtLastError();
+    return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan hybrid launch");
+}
+
+// tile: 0 = 96 KiB staged + 64 KiB in registers (two blocks per SM),
+// 1 = 64 KiB + 32 KiB (three blocks per SM), 2 = 64 KiB + 48 KiB (three
+// blocks per SM), 3 = 96 KiB + 80 KiB (two blocks per SM).
+template <class T, bool INCL, bool REV>
+int run_scan_hybrid_dir(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+{
+    if (c.tile == 0) return launch_scan_hybrid<T, INCL, REV, 6, 4, 2>(sc, s);
+    if (c.tile == 1) return launch_scan_hybrid<T, INCL, REV, 4, 2, 3>(sc, s);
+    if (c.tile == 2) return launch_scan_hybrid<T, INCL, REV, 4, 3, 3>(sc, s);
+    return launch_scan_hybrid<T, INCL, REV, 6, 5, 2>(sc, s);
+}
+
+template <class T, bool INCL>
+int run_scan_hybrid(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
+{
+    if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan hybrid: ept must be 4");
+    if (c.tile < 0 || c.tile > 3) return fail(SKEL_ERR_INVALID_ARG, "scan hybrid: tile must be 0..3");
+    // bulk copies start on 16-byte boundaries: aligned operands, and segments
+    // of a multiple of 4 elements (reverse 1D scans: n % 4 == 0)
+    const int64_t seglen = sc.seg > 0 ? sc.seg : sc.n;
+    if (!aligned16(sc.in) || !aligned16(sc.out) || ((sc.seg > 0 || sc.reverse) && seglen % 4))
+        return fail(SKEL_ERR_UNSUPPORTED, "scan hybrid: 16-byte aligned operands and segments needed");
+    return sc.reverse ? run_scan_hybrid_dir<T, INCL, true>(sc, c, s) : run_scan_hybrid_dir<T, INCL, false>(sc, c, s);
+}
+
 template <class T, bool INCL>
 int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (c.variant == 4) return run_scan_tma<T, INCL>(sc, c, s);
     if (c.variant == 5) return run_scan_big<T, INCL>(sc, c, s);
+    if (c.variant == 7) return run_scan_hybrid<T, INCL>(sc, c, s);
     if (c.variant == 6) return run_scan_ws<T, INCL>(sc, c, s);
     const int v = c.ept > 0 ? c.ept : 4;
     switch (v) {
@@ -1232,19 +1554,19 @@ int run_scan_v(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 
 }  // namespace
 
-int scan_variant_count() { return 7; }
+int scan_variant_count() { return 8; }
 const char *scan_variant_name(int v)
 {
     static const char *names[] = {"reduce_then_scan", "lookback", "one_block", "lookback_block", "lookback_tma",
-                                  "lookback_big", "lookback_ws"};
-    return v >= 0 && v < 7 ? names[v] : "?";
+                                  "lookback_big", "lookback_ws", "lookback_hybrid"};
+    return v >= 0 && v < 8 ? names[v] : "?";
 }
 Choice scan_default() { return Choice{0, 256, 4, 0}; }
 
 int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (sc.n == 0) return SKEL_OK;
-    if (c.variant < 0 || c.variant > 6) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
+    if (c.variant < 0 || c.variant > 7) return fail(SKEL_ERR_INVALID_ARG, "scan: unknown variant");
     if (c.block > 0 && c.block != kBlock) return fail(SKEL_ERR_INVALID_ARG, "scan: block must be 256");
     if (sc.seg > 0 && sc.n % sc.seg) return fail(SKEL_ERR_SHAPE, "scan: n is not a multiple of the segment");
     if (sc.dtype == SKEL_F32)

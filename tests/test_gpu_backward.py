@@ -179,9 +179,9 @@ def test_composed_loss_8192_fd_and_oracle_gradient():
         assert abs(g[i, j] - fd) <= 1e-4 * abs(fd) + 1e-7, (i, j, g[i, j], fd)
 
 
-@pytest.mark.parametrize("n", [4, 4096, 12288, 12292, 16384, 16388, 1_000_000, 1 << 22])
+@pytest.mark.parametrize("n", [4, 4096, 12288, 12292, 16384, 16388, 28672, 40964, 1_000_000, 1 << 22])
 @pytest.mark.parametrize("inclusive", [True, False])
-@pytest.mark.parametrize("variant,tile", [(5, 0), (5, 1), (5, 3), (6, 0), (6, 1)])
+@pytest.mark.parametrize("variant,tile", [(5, 0), (5, 1), (5, 3), (6, 0), (6, 1), (7, 0), (7, 1), (7, 2), (7, 3)])
 def test_scan_bwd_big_tiles(n, inclusive, variant, tile):
     """Reverse scans through the staged big-tile and warp-specialised
     variants (n % 4 == 0)."""
@@ -196,7 +196,7 @@ def test_scan_bwd_big_tiles(n, inclusive, variant, tile):
     assert_prefix_close(to_np(out), ref, ab, f"reverse big n={n}")
 
 
-@pytest.mark.parametrize("variant", [5, 6])
+@pytest.mark.parametrize("variant", [5, 6, 7])
 def test_scan_bwd_big_tiles_rows_and_refusal(variant):
     import torch
     from helpers import forced

@@ -12,11 +12,11 @@ from helpers import dev_empty, dev_tensor, forced, skel, to_np, wrap
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6])   # warp, block, pipelined, wide, warp-specialised
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7])   # warp, block, pipelined, wide, warp-specialised, hybrid
 def test_lookback_wait_runs_out_and_is_reported(variant):
     import torch
     sk = skel()
-    n = 20 * 4096 + 5
+    n = 20 * 40960 + 5                  # at least 20 tiles for every variant (the hybrid's are 40960 elements)
     x = syn.uniform_int(1, n, 0, 100)
     out = dev_empty((n,), torch.int32)
     sk.skel_check_device()

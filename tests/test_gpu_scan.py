@@ -13,9 +13,11 @@ pytestmark = pytest.mark.gpu
 SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 << 20) + 3, 3_000_001]
 # (variant, ept, tile); variant 5: tile bit 0 publishes the tile aggregate
 # early, bit 1 selects 48 KiB tiles; variant 6: tile 0 = four 48 KiB stages,
-# 1 = six 32 KiB stages
+# 1 = six 32 KiB stages; variant 7: tile 0 = 96 KiB staged + 64 KiB in
+# registers, 1 = 64 + 32 KiB, 2 = 64 + 48 KiB, 3 = 96 + 80 KiB
 SCAN_CONFIGS = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (1, 8, 0), (2, 4, 0), (2, 8, 0), (3, 4, 0), (3, 2, 0),
-                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1), (5, 4, 2), (5, 4, 3), (6, 4, 0), (6, 4, 1)]
+                (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1), (5, 4, 2), (5, 4, 3), (6, 4, 0), (6, 4, 1), (7, 4, 0),
+                (7, 4, 1), (7, 4, 2), (7, 4, 3)]
 
 
 def mod32(a):
@@ -33,7 +35,7 @@ def test_scan_i32_exact(variant, ept, tile, n, inclusive, pad):
     dx = dev_tensor(x, pad)
     dout = dev_empty((n,), torch.int32, pad)
     with forced("scan", variant, 0, ept, tile):
-        if variant in (4, 5, 6) and pad % 4:
+        if variant in (4, 5, 6, 7) and pad % 4:
             # bulk copies need 16-byte aligned operands; a forced call does not fall back
             with pytest.raises(sk.SkelError) as e:
                 sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
@@ -91,7 +93,7 @@ def test_scan_rows(variant, rows, cols, inclusive):
         assert np.array_equal(gi[r], mod32(oracle.scan_i32(xi[r], inclusive)))
 
 
-@pytest.mark.parametrize("variant,tile", [(1, 0), (6, 0), (6, 1)])
+@pytest.mark.parametrize("variant,tile", [(1, 0), (6, 0), (6, 1), (7, 0), (7, 1)])
 def test_scan_lookback_repeated_runs_identical_int(variant, tile):
     """Races in the look-back (or, for the warp-specialised variant, in the
     hand-over of stages between its roles) would show up as run-to-run
@@ -110,7 +112,7 @@ def test_scan_lookback_repeated_runs_identical_int(variant, tile):
             assert np.array_equal(to_np(dout), ref)
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7])
 def test_scan_types_interleaved_share_lookback_words(variant):
     """int32 and float32 look-back scans alternate on one stream and reuse the
     same descriptor words; a stale word of one type must never read as a
@@ -131,8 +133,8 @@ def test_scan_types_interleaved_share_lookback_words(variant):
         assert_prefix_close(to_np(of), ref, ab, f"interleaved f32 call {k}")
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6])
-@pytest.mark.parametrize("rows,cols", [(3, 5000), (7, 4096), (64, 1000), (2, 12), (3, 40000)])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7])
+@pytest.mark.parametrize("rows,cols", [(3, 5000), (7, 4096), (64, 1000), (2, 12), (3, 40000), (2, 163840), (3, 200000)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_scan_rows_tma(variant, rows, cols, inclusive):
     """Row-wise scans through the bulk-copy variants (segments of a multiple
@@ -167,3 +169,24 @@ def test_scan_ws_many_ring_turns(tile, inclusive):
     assert np.array_equal(to_np(oi), mod32(oracle.scan_i32(xi, inclusive)))
     ref, ab = oracle.scan_f32(xf, inclusive)
     assert_prefix_close(to_np(of), ref, ab, f"ws f32 2^25 tile={tile}")
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_hybrid_many_tiles_and_ragged_tail(tile, inclusive):
+    """The hybrid-staged variant over 2^25 + 3 elements: thousands of tiles in
+    flight, a last tile that ends inside its register part, and a last group
+    of fewer than four elements."""
+    import torch
+    sk = skel()
+    n = (1 << 25) + 3
+    xi = syn.uniform_int(910 + tile, n, 0, 100)
+    oi = dev_empty((n,), torch.int32)
+    xf = syn.uniform_f32(911 + tile, n)
+    of = dev_empty((n,), torch.float32)
+    with forced("scan", 7, 0, 4, tile):
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xi)), wrap(oi))
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xf)), wrap(of))
+    assert np.array_equal(to_np(oi), mod32(oracle.scan_i32(xi, inclusive)))
+    ref, ab = oracle.scan_f32(xf, inclusive)
+    assert_prefix_close(to_np(of), ref, ab, f"hybrid f32 2^25+3 tile={tile}")

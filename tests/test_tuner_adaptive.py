@@ -69,3 +69,14 @@ def test_tuner_tries_every_variant_the_library_offers():
         tried = {c[0] for c in tune.candidates(name)}
         assert tried == offered, (name, sorted(tried), sorted(offered))
         assert all(sk.skel_variant_name(name, v) != "?" for v in offered)
+
+
+def test_set_table_entry_replaces_or_adds_a_bucket(tmp_path):
+    """The validation's re-decision rewrites exactly one bucket's line of the
+    execution-plan table (or adds it when the bucket was extrapolated)."""
+    p = tmp_path / "t.tbl"
+    p.write_text("# header\n0 3 0 10 0 0 1 256 2 0\n0 3 0 11 0 0 3 256 4 0\n")
+    tune.set_table_entry(str(p), (0, 3, 0, 10, 0, 0), (-1, 0, 0, 0))
+    assert p.read_text().splitlines() == ["# header", "0 3 0 10 0 0 -1 0 0 0", "0 3 0 11 0 0 3 256 4 0"]
+    tune.set_table_entry(str(p), (1, 0, 0, 9, 0, 0), (-1, 0, 0, 0))
+    assert p.read_text().splitlines()[-1] == "1 0 0 9 0 0 -1 0 0 0"
