@@ -105,6 +105,8 @@ def candidates(sk_name: str):
     elif sk_name == "maparray":
         for v in (0, 1, 2, 3):
             yield (v, 256, 0, 0)
+        for e in (4, 8):         # gather: more groups of four in flight per thread (rowdot ignores ept)
+            yield (2, 256, e, 0)
     elif sk_name == "chain2d":
         yield (0, 0, 0, 0)
         for k in (1, 2, 3, 4, 5, 6, 8):
