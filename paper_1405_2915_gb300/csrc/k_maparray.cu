@@ -8,7 +8,9 @@
 //   1 vec4        gather: 16-byte index loads and output stores, four outputs
 //                 per thread; rowdot: one warp per row, 16-byte coalesced
 //                 row loads, warp-shuffle sum.
-//   2 block_row   rowdot only: one block per row, block-tree sum (long rows).
+//   2 block_row   rowdot: one block per row, block-tree sum (long rows);
+//     vec4_multi  gather: vec4 with ept groups of four per thread per step
+//                 (8, 16 or 32 random reads of A in flight per thread).
 //   3 split_row   rowdot only: each row split over several blocks (partials
 //                 in scratch, then a fixed-order combine): few, long rows.
 // A is read through the read-only path; it stays in L1/L2 across rows.
@@ -38,6 +40,40 @@ __global__ void gather_vec4(const float *__restrict__ A, int64_t m, const int32_
         o.z = __ldg(A + clampi((int32_t)k.z, m));
         o.w = __ldg(A + clampi((int32_t)k.w, m));
         dev::st_stream(reinterpret_cast<float4 *>(out) + i, o);
+    }
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n - 4 * nv) out[4 * nv + t] = __ldg(A + clampi(idx[4 * nv + t], m));
+}
+
+// G groups of four indices per thread per step: 4G random reads of A in
+// flight per thread (vec4 keeps four), the index loads and output stores
+// still 16 bytes and coalesced (group g of a step lies one grid stride after
+// group g - 1).
+template <int G>
+__global__ void gather_vec4_multi(const float *__restrict__ A, int64_t m, const int32_t *__restrict__ idx,
+                                  float *__restrict__ out, int64_t n)
+{
+    const int64_t nv = n / 4;
+    const int64_t T = (int64_t)gridDim.x * blockDim.x;
+    const uint4 *idx4 = reinterpret_cast<const uint4 *>(idx);
+    float4 *out4 = reinterpret_cast<float4 *>(out);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < nv; i0 += T * G) {
+        uint4 k[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (i0 + g * T < nv) k[g] = dev::ld_stream(idx4 + i0 + g * T);
+        float4 o[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (i0 + g * T < nv) {
+                o[g].x = __ldg(A + clampi((int32_t)k[g].x, m));
+                o[g].y = __ldg(A + clampi((int32_t)k[g].y, m));
+                o[g].z = __ldg(A + clampi((int32_t)k[g].z, m));
+                o[g].w = __ldg(A + clampi((int32_t)k[g].w, m));
+            }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            if (i0 + g * T < nv) dev::st_stream(out4 + i0 + g * T, o[g]);
     }
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n - 4 * nv) out[4 * nv + t] = __ldg(A + clampi(idx[4 * nv + t], m));
@@ -195,7 +231,7 @@ unsigned grid_for(int64_t work, int block)
 int maparray_variant_count() { return 4; }
 const char *maparray_variant_name(int v)
 {
-    static const char *names[] = {"scalar", "vec4", "block_row", "split_row"};
+    static const char *names[] = {"scalar", "vec4", "block_row / vec4_multi", "split_row"};
     return v >= 0 && v < 4 ? names[v] : "?";
 }
 Choice maparray_default() { return Choice{1, 256, 0, 0}; }
@@ -216,6 +252,19 @@ int launch_maparray(const MapArrayLaunch &ma, const Choice &c, cudaStream_t s)
                 return fail(SKEL_ERR_UNSUPPORTED, "gather vec4: 16-byte aligned operands needed");
             launch_kernel(gather_vec4, grid_for(ceil_div(ma.n, 4), block), block, 0, s, ma.A, ma.m, idx, ma.out, ma.n);
             return check_launch("gather vec4");
+        }
+        if (c.variant == 2) {
+            if (!aligned16(idx) || !aligned16(ma.out))
+                return fail(SKEL_ERR_UNSUPPORTED, "gather vec4 multi: 16-byte aligned operands needed");
+            const int G = c.ept > 0 ? c.ept : 2;
+            const unsigned g = grid_for(ceil_div(ceil_div(ma.n, 4), G), block);
+            switch (G) {
+            case 2: launch_kernel(gather_vec4_multi<2>, g, block, 0, s, ma.A, ma.m, idx, ma.out, ma.n); break;
+            case 4: launch_kernel(gather_vec4_multi<4>, g, block, 0, s, ma.A, ma.m, idx, ma.out, ma.n); break;
+            case 8: launch_kernel(gather_vec4_multi<8>, g, block, 0, s, ma.A, ma.m, idx, ma.out, ma.n); break;
+            default: return fail(SKEL_ERR_INVALID_ARG, "gather vec4 multi: ept (groups per thread) must be 2, 4 or 8");
+            }
+            return check_launch("gather vec4 multi");
         }
         return fail(SKEL_ERR_UNSUPPORTED, "gather: variant not offered");
     }

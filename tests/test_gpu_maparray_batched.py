@@ -10,15 +10,15 @@ from helpers import (SUM_REL, assert_prefix_close, dev_empty, dev_tensor, forced
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant,ept", [(0, 0), (1, 0), (2, 2), (2, 4), (2, 8)])
 @pytest.mark.parametrize("m,n", [(1, 1), (7, 5), (1000, 4099), (1 << 16, 1 << 20), (3, 100_003)])
-def test_gather(variant, m, n):
+def test_gather(variant, ept, m, n):
     import torch
     sk = skel()
     A = syn.uniform_f32(syn.SEED_X, m)
     idx = syn.uniform_int(syn.SEED_IDX, n, -5, m + 5)          # includes out-of-range indices (clamped)
     dout = dev_empty((n,), torch.float32)
-    with forced("maparray", variant):
+    with forced("maparray", variant, 0, ept):
         sk.skel_maparray("gather", wrap(dev_tensor(A)), wrap(dev_tensor(idx)), wrap(dout))
     assert np.array_equal(to_np(dout).astype(np.float64), oracle.gather_f32(A, idx))   # a copy: exact
 
