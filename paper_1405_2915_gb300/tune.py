@@ -127,6 +127,8 @@ def candidates(sk_name: str):
         yield (3, 256, 4, 0)
         yield (5, 256, 4, 0)
         yield (5, 256, 8, 0)
+        for t in range(4):       # the instances as one flat segmented scan, four tile shapes
+            yield (6, 256, 4, t)
 
 
 def grid_side(n: int) -> int:

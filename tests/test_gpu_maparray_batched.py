@@ -60,25 +60,50 @@ def check_batched(v, off, res, scan, inclusive):
         assert_prefix_close(scan, ref, ab, "batched scan")
 
 
-@pytest.mark.parametrize("variant,ept", [(0, 4), (1, 4), (0, 2), (0, 8), (2, 4), (1, 8), (3, 4), (4, 4), (4, 8), (5, 4),
-                                         (5, 8)])
+@pytest.mark.parametrize("variant,ept,tile", [(0, 4, 0), (1, 4, 0), (0, 2, 0), (0, 8, 0), (2, 4, 0), (1, 8, 0), (3, 4, 0),
+                                              (4, 4, 0), (4, 8, 0), (5, 4, 0), (5, 8, 0), (6, 4, 0), (6, 4, 1), (6, 4, 2),
+                                              (6, 4, 3)])
 @pytest.mark.parametrize("inclusive", [True, False])
-def test_batched_small_mixed(variant, ept, inclusive):
-    """Empty, tiny, unaligned and multi-tile instances mixed."""
+def test_batched_small_mixed(variant, ept, tile, inclusive):
+    """Empty, tiny, unaligned and multi-tile instances mixed (for the flat
+    variant's tiles of 24576 to 40960 elements: instances that cross one and
+    two tile boundaries, a start exactly on a 32768-element boundary, and
+    trailing empties)."""
     import torch
     sk = skel()
-    lens = np.array([0, 1, 3, 4, 5, 0, 64, 4095, 4096, 4097, 13, 20000, 0, 1, 70001, 2], np.int64)
+    lens = np.array([0, 1, 3, 4, 5, 0, 64, 4095, 4096, 4097, 13, 20000, 0, 1, 70001, 2, 28690,   # next starts at 4 x 32768
+                     3, 65536, 0, 0], np.int64)
     off = syn.csr_offsets(lens)
     v = syn.uniform_f32(syn.SEED_BATCH_VAL, int(off[-1]))
     res = torch.full((len(lens),), -7.0, device="cuda")
     sc = torch.full((int(off[-1]),), -7.0, device="cuda")
-    with forced("batched", variant, 0, ept):
+    with forced("batched", variant, 0, ept, tile):
         sk.skel_batched(wrap(dev_tensor(v)), wrap(dev_tensor(off)), wrap(res), wrap(sc), inclusive)
     sk.skel_check_device()
     check_batched(v, off, to_np(res), to_np(sc), inclusive)
 
 
-@pytest.mark.parametrize("variant", [0, 3, 5])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_batched_flat_tile_boundaries(tile, inclusive):
+    """The flat variant when instances start exactly on tile boundaries
+    (110592 = 3 x 36864, 122880 = 3 x 40960 = 5 x 24576) and when the array
+    is a whole number of tiles (no partial tile is launched)."""
+    import torch
+    sk = skel()
+    for lens in ([0, 110592, 12288, 0], [110592, 12288, 7, 0, 1]):
+        lens = np.array(lens, np.int64)
+        off = syn.csr_offsets(lens)
+        v = syn.uniform_f32(syn.SEED_BATCH_VAL, int(off[-1]))
+        res = torch.full((len(lens),), -7.0, device="cuda")
+        sc = torch.full((int(off[-1]),), -7.0, device="cuda")
+        with forced("batched", 6, 0, 4, tile):
+            sk.skel_batched(wrap(dev_tensor(v)), wrap(dev_tensor(off)), wrap(res), wrap(sc), inclusive)
+        sk.skel_check_device()
+        check_batched(v, off, to_np(res), to_np(sc), inclusive)
+
+
+@pytest.mark.parametrize("variant", [0, 3, 5, 6])
 def test_batched_only_reduce_and_only_scan(variant):
     import torch
     sk = skel()
@@ -99,7 +124,7 @@ def _only_reduce_only_scan(sk, torch):
     check_batched(v, off, to_np(res), to_np(sc), True)
 
 
-@pytest.mark.parametrize("variant", [0, 3, 5])
+@pytest.mark.parametrize("variant", [0, 3, 5, 6])
 def test_batched_full_workload_and_graph_plan(variant):
     """4096 instances, log-uniform lengths in [64, 2^20] (~4.4e8 elements):
     direct call, captured plan replayed twice, and per-instance calls on a
@@ -145,7 +170,7 @@ def _full_workload(sk, torch):
         view.close()
 
 
-@pytest.mark.parametrize("variant", [-1, 5])
+@pytest.mark.parametrize("variant", [-1, 5, 6])
 def test_batched_rejects_bad_offsets(variant):
     import torch
     sk = skel()
