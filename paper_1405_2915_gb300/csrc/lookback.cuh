@@ -45,9 +45,14 @@ struct Pair {
 __device__ __forceinline__ Pair operator+(const Pair &a, const Pair &b) { return Pair(a.s + b.s, a.q + b.q); }
 
 template <class CT> __device__ __forceinline__ CT shfl_xor_ct(CT v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+template <class CT> __device__ __forceinline__ CT shfl_ct(CT v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 template <> __device__ __forceinline__ Pair shfl_xor_ct<Pair>(Pair v, int o)
 {
     return Pair(__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.q, o));
+}
+template <> __device__ __forceinline__ Pair shfl_ct<Pair>(Pair v, int src)
+{
+    return Pair(__shfl_sync(0xffffffffu, v.s, src), __shfl_sync(0xffffffffu, v.q, src));
 }
 
 template <class CT> struct Codec;
@@ -177,8 +182,18 @@ __device__ __forceinline__ CT lookback(int64_t tile, int64_t first, CT agg, Look
         }
         const unsigned lim = incl_mask ? (((incl_mask & (0u - incl_mask)) << 1) - 1u) : 0xffffffffu;
         if (!((lim >> lane) & 1u) || status == 0) val = CT(0);
+        if (sizeof(CT) == 4) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) val = val + shfl_xor_ct(val, o);
+            for (int o = 16; o > 0; o >>= 1) val = val + shfl_xor_ct(val, o);
+        } else {
+            // float64 carries: a butterfly over the lanes up to the nearest
+            // prefix only (usually a few; float64 adds are slow on this GPU),
+            // then lane 0's sum to all lanes
+            const int span = 32 - __clz(lim);   // lanes 0..span-1 take part
+            for (int o = 16; o > 0; o >>= 1)
+                if (o < span) val = val + shfl_xor_ct(val, o);   // warp-uniform
+            val = shfl_ct(val, 0);
+        }
         excl = excl + val;
         if (incl_mask) break;
         pred -= 32;

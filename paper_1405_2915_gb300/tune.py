@@ -92,6 +92,8 @@ def candidates(sk_name: str):
             yield (6, 256, 4, t)
         for t in (0, 1, 2, 3):   # hybrid-staged tiles: 96 + 64, 64 + 32, 64 + 48, 96 + 80 KiB
             yield (7, 256, 4, t)
+        for t in (0, 1, 2, 3):   # aggregators and re-reading scanners: ring tiles + scanners 6 + 6, 4 + 8, 6 + 8, 5 + 8
+            yield (8, 256, 4, t)
     elif sk_name == "mapoverlap2d":
         yield (0, 256, 0, 0)
         yield (1, 256, 0, 0)

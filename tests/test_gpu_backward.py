@@ -181,7 +181,8 @@ def test_composed_loss_8192_fd_and_oracle_gradient():
 
 @pytest.mark.parametrize("n", [4, 4096, 12288, 12292, 16384, 16388, 28672, 40964, 1_000_000, 1 << 22])
 @pytest.mark.parametrize("inclusive", [True, False])
-@pytest.mark.parametrize("variant,tile", [(5, 0), (5, 1), (5, 3), (6, 0), (6, 1), (7, 0), (7, 1), (7, 2), (7, 3)])
+@pytest.mark.parametrize("variant,tile", [(5, 0), (5, 1), (5, 3), (6, 0), (6, 1), (7, 0), (7, 1), (7, 2), (7, 3), (8, 0),
+                                          (8, 1), (8, 2), (8, 3)])
 def test_scan_bwd_big_tiles(n, inclusive, variant, tile):
     """Reverse scans through the staged big-tile and warp-specialised
     variants (n % 4 == 0)."""
@@ -213,4 +214,22 @@ def test_scan_bwd_big_tiles_rows_and_refusal(variant):
         bad = dev_empty((4099,), torch.float32)
         with pytest.raises(sk.SkelError) as e:   # reverse 1D scans need n % 4 == 0 here
             sk.skel_scan_bwd("add", True, wrap(dev_tensor(syn.uniform_f32(12, 4099))), wrap(bad))
+        assert e.value.code == -4
+
+
+def test_scan_bwd_reread_refusals():
+    """The re-reading variant runs reverse scans of one segment with n % 4 == 0
+    and refuses the rest before any launch."""
+    import torch
+    from helpers import forced
+    sk = skel()
+    with forced("scan", 8):
+        for n in (4099, 2):
+            bad = dev_empty((n,), torch.float32)
+            with pytest.raises(sk.SkelError) as e:
+                sk.skel_scan_bwd("add", True, wrap(dev_tensor(syn.uniform_f32(12, n))), wrap(bad))
+            assert e.value.code == -4
+        g = syn.uniform_f32(13, 3 * 4096).reshape(3, 4096)
+        with pytest.raises(sk.SkelError) as e:
+            sk.skel_scan_bwd("add", True, wrap(dev_tensor(g)), wrap(dev_empty((3, 4096), torch.float32)))
         assert e.value.code == -4

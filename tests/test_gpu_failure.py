@@ -12,7 +12,7 @@ from helpers import dev_empty, dev_tensor, forced, skel, to_np, wrap
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7])   # warp, block, pipelined, wide, warp-specialised, hybrid
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7, 8])   # warp, block, pipelined, wide, warp-specialised, hybrid, re-read
 def test_lookback_wait_runs_out_and_is_reported(variant):
     import torch
     sk = skel()

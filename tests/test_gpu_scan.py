@@ -14,10 +14,11 @@ SIZES = [1, 2, 3, 4, 5, 31, 1023, 1024, 1025, 4095, 4096, 4097, 8193, 65537, (1 
 # (variant, ept, tile); variant 5: tile bit 0 publishes the tile aggregate
 # early, bit 1 selects 48 KiB tiles; variant 6: tile 0 = four 48 KiB stages,
 # 1 = six 32 KiB stages; variant 7: tile 0 = 96 KiB staged + 64 KiB in
-# registers, 1 = 64 + 32 KiB, 2 = 64 + 48 KiB, 3 = 96 + 80 KiB
+# registers, 1 = 64 + 32 KiB, 2 = 64 + 48 KiB, 3 = 96 + 80 KiB; variant 8:
+# ring tiles + scanner warps 0 = 6 + 6, 1 = 4 + 8, 2 = 6 + 8, 3 = 5 + 8
 SCAN_CONFIGS = [(0, 4, 0), (0, 2, 0), (1, 4, 0), (1, 2, 0), (1, 8, 0), (2, 4, 0), (2, 8, 0), (3, 4, 0), (3, 2, 0),
                 (3, 8, 0), (4, 4, 0), (5, 4, 0), (5, 4, 1), (5, 4, 2), (5, 4, 3), (6, 4, 0), (6, 4, 1), (7, 4, 0),
-                (7, 4, 1), (7, 4, 2), (7, 4, 3)]
+                (7, 4, 1), (7, 4, 2), (7, 4, 3), (8, 4, 0), (8, 4, 1), (8, 4, 2), (8, 4, 3)]
 
 
 def mod32(a):
@@ -35,7 +36,7 @@ def test_scan_i32_exact(variant, ept, tile, n, inclusive, pad):
     dx = dev_tensor(x, pad)
     dout = dev_empty((n,), torch.int32, pad)
     with forced("scan", variant, 0, ept, tile):
-        if variant in (4, 5, 6, 7) and pad % 4:
+        if variant in (4, 5, 6, 7, 8) and pad % 4:
             # bulk copies need 16-byte aligned operands; a forced call does not fall back
             with pytest.raises(sk.SkelError) as e:
                 sk.skel_scan("add", inclusive, wrap(dx), wrap(dout))
@@ -93,7 +94,7 @@ def test_scan_rows(variant, rows, cols, inclusive):
         assert np.array_equal(gi[r], mod32(oracle.scan_i32(xi[r], inclusive)))
 
 
-@pytest.mark.parametrize("variant,tile", [(1, 0), (6, 0), (6, 1), (7, 0), (7, 1)])
+@pytest.mark.parametrize("variant,tile", [(1, 0), (6, 0), (6, 1), (7, 0), (7, 1), (8, 0), (8, 1)])
 def test_scan_lookback_repeated_runs_identical_int(variant, tile):
     """Races in the look-back (or, for the warp-specialised variant, in the
     hand-over of stages between its roles) would show up as run-to-run
@@ -112,7 +113,7 @@ def test_scan_lookback_repeated_runs_identical_int(variant, tile):
             assert np.array_equal(to_np(dout), ref)
 
 
-@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [1, 3, 4, 5, 6, 7, 8])
 def test_scan_types_interleaved_share_lookback_words(variant):
     """int32 and float32 look-back scans alternate on one stream and reuse the
     same descriptor words; a stale word of one type must never read as a
@@ -190,3 +191,37 @@ def test_scan_hybrid_many_tiles_and_ragged_tail(tile, inclusive):
     assert np.array_equal(to_np(oi), mod32(oracle.scan_i32(xi, inclusive)))
     ref, ab = oracle.scan_f32(xf, inclusive)
     assert_prefix_close(to_np(of), ref, ab, f"hybrid f32 2^25+3 tile={tile}")
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_reread_many_tiles_and_ragged_tail(tile, inclusive):
+    """The re-reading variant over 2^25 + 3 elements: every persistent block
+    goes round its ring of tiles many times, the queue to the scanner warps
+    fills, and the last tile is partial with a last group of three."""
+    import torch
+    sk = skel()
+    n = (1 << 25) + 3
+    xi = syn.uniform_int(920 + tile, n, 0, 100)
+    oi = dev_empty((n,), torch.int32)
+    xf = syn.uniform_f32(921 + tile, n)
+    of = dev_empty((n,), torch.float32)
+    with forced("scan", 8, 0, 4, tile):
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xi)), wrap(oi))
+        sk.skel_scan("add", inclusive, wrap(dev_tensor(xf)), wrap(of))
+    assert np.array_equal(to_np(oi), mod32(oracle.scan_i32(xi, inclusive)))
+    ref, ab = oracle.scan_f32(xf, inclusive)
+    assert_prefix_close(to_np(of), ref, ab, f"reread f32 2^25+3 tile={tile}")
+
+
+def test_scan_reread_refuses_rows():
+    """One segment only: a forced row-wise call is refused before any launch
+    (an unforced one falls back to the default variant)."""
+    import torch
+    sk = skel()
+    x = syn.uniform_f32(44, 3 * 5000).reshape(3, 5000)
+    dout = dev_empty((3, 5000), torch.float32)
+    with forced("scan", 8):
+        with pytest.raises(sk.SkelError) as e:
+            sk.skel_scan("add", True, wrap(dev_tensor(x)), wrap(dout))
+        assert e.value.code == -4
