@@ -5,7 +5,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "skel.h"
 
@@ -34,6 +36,36 @@ struct DeviceInfo {
     size_t l2_bytes;
 };
 const DeviceInfo &device_info();  // of the current device
+
+// Opts kern in to dyn bytes of dynamic shared memory and returns its resident
+// blocks per SM at that size (0 or less: it does not fit), set up once per
+// kernel, block size and device, so that no host query sits between the
+// launches of a call.
+template <class K>
+int kernel_occupancy(K kern, int threads, int dyn)
+{
+    struct Entry {
+        const void *k;
+        int dev, threads, dyn, occ;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const Entry &e : cache)
+        if (e.k == reinterpret_cast<const void *>(kern) && e.dev == dev && e.threads == threads && e.dyn == dyn)
+            return e.occ;
+    int occ = 0;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        occ = -1;
+    }
+    cache.push_back(Entry{reinterpret_cast<const void *>(kern), dev, threads, dyn, occ});
+    return occ;
+}
 
 // ------------------------------------------------------- scratch memory --
 // Layout of a scratch block: a 256-byte control block, a region of look-back

@@ -1562,10 +1562,10 @@ int run_scan_hybrid(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 // scanner only waits for its predecessors, all of which have prefixes.
 // An aggregator waits only for its own copies and for room in its block's
 // queue, which its scanners free without waiting on anything.  Every wait
-// is bounded; one that runs out records kErrTimeout and the call's abort tag,
-// which ends every other waiter of the call; blocks still draw their last
-// ticket so the ticket counter resets, and wait (bounded) for their copies
-// before leaving.
+// is bounded;
+// one that runs out records kErrTimeout and the call's abort tag, which ends
+// every other waiter of the call; blocks wait (bounded) for their copies
+// before leaving, and the last block to leave resets the ticket counter.
 constexpr int kRrTE = 4096;   // elements per tile
 constexpr int kRrAggW = 2;    // aggregator warps
 constexpr int kRrQueue = 16;  // queue entries per block
@@ -1651,7 +1651,6 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
         // by a plain arrival (it is summed from global memory), or the end mark
         auto start = [&](int slot, uint32_t t) {
             if (s_stop || (int64_t)t >= ntiles) {
-                if (!s_stop && (int64_t)t == ntiles + (int64_t)gridDim.x - 1) ctl->ticket = 0u;   // every block drew its last
                 s_stop = 1;
                 slot_tile[slot] = ntiles;
                 return;
@@ -1667,27 +1666,27 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          :: "r"(smem_u32(dyn + slot * TB)), "l"(in + tile_start(t)), "r"(TB), "r"(b) : "memory");
         };
-        auto draw = [&]() -> uint32_t { return s_stop ? 0u : atomicAdd(&ctl->ticket, 1u); };
-        if (threadIdx.x == 0)
-            for (int s = 0; s < R; ++s) start(s, draw());
+        if (threadIdx.x == 0) {
+            uint32_t first[R];
+#pragma unroll
+            for (int s = 0; s < R; ++s) first[s] = atomicAdd(&ctl->ticket, 1u);   // all in flight at once
+#pragma unroll
+            for (int s = 0; s < R; ++s) start(s, first[s]);
+        }
         group_sync(kRrBar, NA * 32);
         for (int i = 0;; ++i) {
             const int slot = i % R;
             const uint32_t par = (uint32_t)(i / R) & 1u;
             const int64_t t = slot_tile[slot];
             if (t >= ntiles) break;   // uniform over the aggregators
-            // the slot's next ticket, drawn now so its round trip overlaps the wait and the sum
-            uint32_t next = 0;
-            if (threadIdx.x == 0) next = draw();
+            // the slot's next ticket, drawn now so that its round trip overlaps
+            // the wait and the sum (drawn further ahead, a tile would be held
+            // back while later tiles look back at it)
+            uint32_t next = (uint32_t)ntiles;
+            if (threadIdx.x == 0 && !s_stop) next = atomicAdd(&ctl->ticket, 1u);
             const bool done = wait_phase(&ring_full[slot], par);
             if (!group_and(kRrBar, NA * 32, done)) {   // a copy never landed
-                if (threadIdx.x == 0) {
-                    give_up();
-                    if (!s_stop && (int64_t)next >= ntiles) {   // the ticket drawn above was past the end
-                        if ((int64_t)next == ntiles + (int64_t)gridDim.x - 1) ctl->ticket = 0u;
-                        s_stop = 1;
-                    }
-                }
+                if (threadIdx.x == 0) give_up();
                 // drain every slot still waiting on a copy (parity of its pending phase)
                 for (int j = 0; j < R; ++j) {
                     if (slot_tile[j] >= ntiles) continue;
@@ -1751,16 +1750,14 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
             // slot_tile[] is read again only after later barriers of this group
         }
         if (threadIdx.x == 0) {
-            // the tickets after a failure: draw up to the first one past the end, so the counter resets
-            for (uint32_t k = 0; k < (1u << 24) && !s_stop; ++k) {
-                const uint32_t t = atomicAdd(&ctl->ticket, 1u);
-                if ((int64_t)t >= ntiles) {
-                    if ((int64_t)t == ntiles + (int64_t)gridDim.x - 1) ctl->ticket = 0u;
-                    s_stop = 1;
-                }
-            }
             __threadfence_block();
             *(volatile int *)&a_done = 1;
+            // the last block to stop drawing tickets resets the counter
+            __threadfence();
+            if (atomicAdd(&ctl->exited, 1u) == gridDim.x - 1) {
+                ctl->ticket = 0u;
+                ctl->exited = 0u;
+            }
         }
         return;
     }
@@ -1888,11 +1885,8 @@ int launch_scan_rr(const ScanLaunch &sc, cudaStream_t s)
     auto kern = scan_rr<T, INCL, REV, R, NC>;
     const int dyn = (R + NC) * kRrTE * (int)sizeof(T);
     const int threads = (kRrAggW + NC) * 32;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    if (e != cudaSuccess) return fail_cuda(e, "scan rr: shared memory opt-in");
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, dyn);
-    if (e != cudaSuccess || occ < 1) return fail(SKEL_ERR_UNSUPPORTED, "scan rr: kernel does not fit an SM");
+    const int occ = kernel_occupancy(kern, threads, dyn);
+    if (occ < 1) return fail(SKEL_ERR_UNSUPPORTED, "scan rr: kernel does not fit an SM");
     const int64_t grid = (int64_t)device_info().sms * occ;
     Scratch scr{};
     int rc = get_scratch(s, 0, 2 * (size_t)ntiles, &scr);
@@ -1901,7 +1895,7 @@ int launch_scan_rr(const ScanLaunch &sc, cudaStream_t s)
     const DebugKnobs k = debug_knobs();
     launch_kernel(kern, (unsigned)grid, threads, (size_t)dyn, s, in, out, sc.n, ntiles, d, scr.ctl, scr.epoch,
                   k.scan_skip_publish_tile, k.wait_limit_ns);
-    e = cudaPeekAtLastError();
+    const cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan rr launch");
 }
 

@@ -131,6 +131,8 @@ def candidates(sk_name: str):
         yield (5, 256, 8, 0)
         for t in range(4):       # the instances as one flat segmented scan, four tile shapes
             yield (6, 256, 4, t)
+        for t in (0, 1):         # flat, aggregators and re-reading scanners: ring tiles + scanners 6 + 6, 4 + 8
+            yield (7, 256, 4, t)
 
 
 def grid_side(n: int) -> int:

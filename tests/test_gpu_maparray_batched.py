@@ -62,7 +62,7 @@ def check_batched(v, off, res, scan, inclusive):
 
 @pytest.mark.parametrize("variant,ept,tile", [(0, 4, 0), (1, 4, 0), (0, 2, 0), (0, 8, 0), (2, 4, 0), (1, 8, 0), (3, 4, 0),
                                               (4, 4, 0), (4, 8, 0), (5, 4, 0), (5, 8, 0), (6, 4, 0), (6, 4, 1), (6, 4, 2),
-                                              (6, 4, 3)])
+                                              (6, 4, 3), (7, 4, 0), (7, 4, 1)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_batched_small_mixed(variant, ept, tile, inclusive):
     """Empty, tiny, unaligned and multi-tile instances mixed (for the flat
@@ -83,12 +83,13 @@ def test_batched_small_mixed(variant, ept, tile, inclusive):
     check_batched(v, off, to_np(res), to_np(sc), inclusive)
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant,tile", [(6, 0), (6, 1), (6, 2), (6, 3), (7, 0), (7, 1)])
 @pytest.mark.parametrize("inclusive", [True, False])
-def test_batched_flat_tile_boundaries(tile, inclusive):
-    """The flat variant when instances start exactly on tile boundaries
-    (110592 = 3 x 36864, 122880 = 3 x 40960 = 5 x 24576) and when the array
-    is a whole number of tiles (no partial tile is launched)."""
+def test_batched_flat_tile_boundaries(variant, tile, inclusive):
+    """The flat variants when instances start exactly on tile boundaries
+    (110592 = 3 x 36864 = 27 x 4096, 122880 = 3 x 40960 = 5 x 24576 =
+    30 x 4096) and when the array is a whole number of tiles (no partial
+    tile)."""
     import torch
     sk = skel()
     for lens in ([0, 110592, 12288, 0], [110592, 12288, 7, 0, 1]):
@@ -97,13 +98,13 @@ def test_batched_flat_tile_boundaries(tile, inclusive):
         v = syn.uniform_f32(syn.SEED_BATCH_VAL, int(off[-1]))
         res = torch.full((len(lens),), -7.0, device="cuda")
         sc = torch.full((int(off[-1]),), -7.0, device="cuda")
-        with forced("batched", 6, 0, 4, tile):
+        with forced("batched", variant, 0, 4, tile):
             sk.skel_batched(wrap(dev_tensor(v)), wrap(dev_tensor(off)), wrap(res), wrap(sc), inclusive)
         sk.skel_check_device()
         check_batched(v, off, to_np(res), to_np(sc), inclusive)
 
 
-@pytest.mark.parametrize("variant", [0, 3, 5, 6])
+@pytest.mark.parametrize("variant", [0, 3, 5, 6, 7])
 def test_batched_only_reduce_and_only_scan(variant):
     import torch
     sk = skel()
@@ -124,7 +125,7 @@ def _only_reduce_only_scan(sk, torch):
     check_batched(v, off, to_np(res), to_np(sc), True)
 
 
-@pytest.mark.parametrize("variant", [0, 3, 5, 6])
+@pytest.mark.parametrize("variant", [0, 3, 5, 6, 7])
 def test_batched_full_workload_and_graph_plan(variant):
     """4096 instances, log-uniform lengths in [64, 2^20] (~4.4e8 elements):
     direct call, captured plan replayed twice, and per-instance calls on a
@@ -170,7 +171,7 @@ def _full_workload(sk, torch):
         view.close()
 
 
-@pytest.mark.parametrize("variant", [-1, 5, 6])
+@pytest.mark.parametrize("variant", [-1, 5, 6, 7])
 def test_batched_rejects_bad_offsets(variant):
     import torch
     sk = skel()
