@@ -1595,10 +1595,10 @@ template <> struct RrCarry<float> {
     }
 };
 
-template <class T, bool INCL, bool REV, int R, int NC>
+template <class T, bool INCL, bool REV, bool ROWS, int R, int NC>
 __global__ void __launch_bounds__((kRrAggW + NC) * 32, 1)
-scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles, LookbackDesc d, Control *ctl,
-        uint32_t epoch, int64_t skip_tile, uint64_t limit_ns)
+scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t seglen, int64_t tps, int64_t ntiles, LookbackDesc d,
+        Control *ctl, uint32_t epoch, int64_t skip_tile, uint64_t limit_ns)
 {
     using CT = typename ScanTypes<T>::CT;
     using V4 = typename ScanTypes<T>::V4;
@@ -1614,11 +1614,24 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
     __shared__ T a_part[NA];
     __shared__ int q_tail, q_claim, q_read, a_done, s_stop;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nfull = n / TE;
+    // tile t is tile t % tps of segment t / tps (ROWS: rows of seglen
+    // elements; else one segment and no division on the tile's path)
+    auto seg_of = [&](int64_t t) -> int64_t { return ROWS ? (int64_t)((uint32_t)t / (uint32_t)tps) : 0; };
+    auto first_of = [&](int64_t t) -> int64_t { return seg_of(t) * tps; };
+    auto tile_len = [&](int64_t t) -> int {
+        const int64_t e0 = (t - seg_of(t) * tps) * TE;
+        return seglen - e0 < TE ? (int)(seglen - e0) : TE;
+    };
     // physical index of logical element e of tile t
-    auto phys = [&](int64_t t, int64_t e) -> int64_t { return REV ? n - 1 - t * TE - e : t * TE + e; };
+    auto phys = [&](int64_t t, int64_t e) -> int64_t {
+        const int64_t sg = seg_of(t), e0 = (t - sg * tps) * TE;
+        return REV ? (sg + 1) * seglen - 1 - e0 - e : sg * seglen + e0 + e;
+    };
     // first physical element of whole tile t
-    auto tile_start = [&](int64_t t) -> int64_t { return REV ? n - (t + 1) * TE : t * TE; };
+    auto tile_start = [&](int64_t t) -> int64_t {
+        const int64_t sg = seg_of(t), e0 = (t - sg * tps) * TE;
+        return REV ? (sg + 1) * seglen - e0 - TE : sg * seglen + e0;
+    };
     auto gave_up = [&]() { return dev::ld_volatile(&ctl->abort) == epoch; };
     auto give_up = [&]() {
         atomicOr(&ctl->error, kErrTimeout);
@@ -1657,7 +1670,7 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
             }
             slot_tile[slot] = t;
             const uint32_t b = smem_u32(&ring_full[slot]);
-            if ((int64_t)t >= nfull) {
+            if (tile_len(t) < TE) {
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
                 return;
             }
@@ -1699,7 +1712,8 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
             }
             // the tile sum: four accumulators per thread, each over groups of four (a shallow sum)
             T acc[4] = {T(0), T(0), T(0), T(0)};
-            if (t < nfull) {
+            const int len = tile_len(t);
+            if (len == TE) {
                 const V4 *src = reinterpret_cast<const V4 *>(dyn + slot * TB);
                 constexpr int PER = TE / 4 / (NA * 32);   // groups of four per thread
                 static_assert(PER % 4 == 0, "whole rounds of the four accumulators");
@@ -1709,7 +1723,6 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
                     acc[k & 3] = acc[k & 3] + ((q.x + q.y) + (q.z + q.w));
                 }
             } else {
-                const int len = (int)(n - t * TE);
                 for (int k0 = 0; k0 * NA * 32 * 4 < len; k0 += 4) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -1727,8 +1740,8 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
                 T agg = a_part[0];
 #pragma unroll
                 for (int j = 1; j < NA; ++j) agg = agg + a_part[j];
-                if (t != skip_tile) {
-                    if (t == 0) dev::Codec<CT>::put(d.incl, (CT)agg, epoch);
+                if (t != skip_tile) {   // a segment's first tile: its sum is its inclusive prefix
+                    if (t == first_of(t)) dev::Codec<CT>::put(d.incl + t * W, (CT)agg, epoch);
                     else dev::Codec<CT>::put(d.agg + t * W, (CT)agg, epoch);
                 }
                 const uint64_t t0 = dev::globaltimer();
@@ -1790,7 +1803,7 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
             atomicAdd(&q_read, 1);
             // the tile again, into this warp's buffer (whole tiles; the partial one is read directly)
             const uint32_t b = smem_u32(&buf_full[cw]);
-            if (t < nfull) {
+            if (tile_len(t) == TE) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(TB) : "memory");
                 asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
@@ -1801,8 +1814,9 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
         }
         t = __shfl_sync(0xffffffffu, t, 0);
         agg = __shfl_sync(0xffffffffu, agg, 0);
-        const CT excl = dev::lookback<CT>(t, 0, (CT)agg, d, epoch, ctl, limit_ns, false);
-        if (lane == 0 && t != 0 && t != skip_tile) dev::Codec<CT>::put(d.incl + t * W, excl + (CT)agg, epoch);
+        const int64_t first = first_of(t);
+        const CT excl = dev::lookback<CT>(t, first, (CT)agg, d, epoch, ctl, limit_ns, false);
+        if (lane == 0 && t != first && t != skip_tile) dev::Codec<CT>::put(d.incl + t * W, excl + (CT)agg, epoch);
         const bool landed = __all_sync(0xffffffffu, wait_phase(&buf_full[cw], cpar));
         cpar ^= 1u;
         if (!landed) {   // the copy never landed: record, wait once more (bounded), stop taking tiles
@@ -1815,7 +1829,8 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
         // the scan: blocks of 512 elements from the running prefix, four
         // 128-element warp scans in the element type inside each block
         RrCarry<T> carry(excl);
-        if (t < nfull) {
+        const int len = tile_len(t);
+        if (len == TE) {
             const V4 *src = reinterpret_cast<const V4 *>(buf);
             V4 *dst = reinterpret_cast<V4 *>(out + tile_start(t));
 #pragma unroll 1
@@ -1844,8 +1859,7 @@ scan_rr(const T *__restrict__ in, T *__restrict__ out, int64_t n, int64_t ntiles
                 }
                 carry.add(loc);
             }
-        } else {   // the partial last tile, element by element
-            const int len = (int)(n - t * TE);
+        } else {   // a segment's partial last tile, element by element
 #pragma unroll 1
             for (int blk = 0; blk * 512 < len; ++blk) {
                 const T base = carry.base();
@@ -1880,9 +1894,10 @@ int launch_scan_rr(const ScanLaunch &sc, cudaStream_t s)
 {
     const T *in = static_cast<const T *>(sc.in);
     T *out = static_cast<T *>(sc.out);
-    const int64_t ntiles = ceil_div(sc.n, (int64_t)kRrTE);
+    const int64_t seglen = sc.seg > 0 ? sc.seg : sc.n, tps = ceil_div(seglen, (int64_t)kRrTE);
+    const int64_t ntiles = tps * (sc.n / seglen);
     if (ntiles > 0x7fffffffLL) return fail(SKEL_ERR_SHAPE, "scan: too many tiles");
-    auto kern = scan_rr<T, INCL, REV, R, NC>;
+    auto kern = seglen < sc.n ? scan_rr<T, INCL, REV, true, R, NC> : scan_rr<T, INCL, REV, false, R, NC>;
     const int dyn = (R + NC) * kRrTE * (int)sizeof(T);
     const int threads = (kRrAggW + NC) * 32;
     const int occ = kernel_occupancy(kern, threads, dyn);
@@ -1893,7 +1908,7 @@ int launch_scan_rr(const ScanLaunch &sc, cudaStream_t s)
     if (rc) return rc;
     LookbackDesc d{scr.words, scr.words + ntiles};
     const DebugKnobs k = debug_knobs();
-    launch_kernel(kern, (unsigned)grid, threads, (size_t)dyn, s, in, out, sc.n, ntiles, d, scr.ctl, scr.epoch,
+    launch_kernel(kern, (unsigned)grid, threads, (size_t)dyn, s, in, out, seglen, tps, ntiles, d, scr.ctl, scr.epoch,
                   k.scan_skip_publish_tile, k.wait_limit_ns);
     const cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "scan rr launch");
@@ -1915,10 +1930,11 @@ int run_scan_rr(const ScanLaunch &sc, const Choice &c, cudaStream_t s)
 {
     if (c.ept > 0 && c.ept != kTmaV) return fail(SKEL_ERR_INVALID_ARG, "scan rr: ept must be 4");
     if (c.tile < 0 || c.tile > 3) return fail(SKEL_ERR_INVALID_ARG, "scan rr: tile must be 0..3");
-    // one segment only; bulk copies start on 16-byte boundaries (reverse: n % 4 == 0)
-    if (sc.seg > 0 && sc.seg != sc.n) return fail(SKEL_ERR_UNSUPPORTED, "scan rr: one segment only");
-    if (!aligned16(sc.in) || !aligned16(sc.out) || (sc.reverse && sc.n % 4))
-        return fail(SKEL_ERR_UNSUPPORTED, "scan rr: 16-byte aligned operands needed");
+    // bulk copies start on 16-byte boundaries: aligned operands, and segments
+    // of a multiple of 4 elements (reverse 1D scans: n % 4 == 0)
+    const int64_t seglen = sc.seg > 0 ? sc.seg : sc.n;
+    if (!aligned16(sc.in) || !aligned16(sc.out) || ((sc.seg > 0 || sc.reverse) && seglen % 4))
+        return fail(SKEL_ERR_UNSUPPORTED, "scan rr: 16-byte aligned operands and segments needed");
     return sc.reverse ? run_scan_rr_dir<T, INCL, true>(sc, c, s) : run_scan_rr_dir<T, INCL, false>(sc, c, s);
 }
 

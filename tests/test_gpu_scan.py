@@ -134,7 +134,7 @@ def test_scan_types_interleaved_share_lookback_words(variant):
         assert_prefix_close(to_np(of), ref, ab, f"interleaved f32 call {k}")
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6, 7])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8])
 @pytest.mark.parametrize("rows,cols", [(3, 5000), (7, 4096), (64, 1000), (2, 12), (3, 40000), (2, 163840), (3, 200000)])
 @pytest.mark.parametrize("inclusive", [True, False])
 def test_scan_rows_tma(variant, rows, cols, inclusive):
@@ -214,13 +214,26 @@ def test_scan_reread_many_tiles_and_ragged_tail(tile, inclusive):
     assert_prefix_close(to_np(of), ref, ab, f"reread f32 2^25+3 tile={tile}")
 
 
-def test_scan_reread_refuses_rows():
-    """One segment only: a forced row-wise call is refused before any launch
-    (an unforced one falls back to the default variant)."""
+@pytest.mark.parametrize("tile", [0, 2])
+@pytest.mark.parametrize("inclusive", [True, False])
+def test_scan_reread_rows_and_refusal(tile, inclusive):
+    """Row-wise scans through the re-reading variant: rows of whole tiles
+    (8192 = 2 x 4096, as in the composed loss), a partial tile per row, and a
+    row length that is not a multiple of 4 (refused before any launch; an
+    unforced call falls back)."""
     import torch
     sk = skel()
-    x = syn.uniform_f32(44, 3 * 5000).reshape(3, 5000)
-    dout = dev_empty((3, 5000), torch.float32)
+    for rows, cols in [(64, 8192), (5, 12300), (9, 100)]:
+        x = syn.uniform_f32(45 + cols, rows * cols).reshape(rows, cols)
+        dout = dev_empty((rows, cols), torch.float32)
+        with forced("scan", 8, 0, 4, tile):
+            sk.skel_scan("add", inclusive, wrap(dev_tensor(x)), wrap(dout))
+        g = to_np(dout)
+        for r in range(rows):
+            ref, ab = oracle.scan_f32(x[r], inclusive)
+            assert_prefix_close(g[r], ref, ab, f"row {r} of {rows} x {cols}")
+    x = syn.uniform_f32(44, 3 * 4097).reshape(3, 4097)
+    dout = dev_empty((3, 4097), torch.float32)
     with forced("scan", 8):
         with pytest.raises(sk.SkelError) as e:
             sk.skel_scan("add", True, wrap(dev_tensor(x)), wrap(dout))
