@@ -492,10 +492,11 @@ const char *skel_variant_name(int skeleton, int variant);
  * computed nothing), SKEL_OK otherwise.  Clears the recorded status. */
 int skel_check_device(void *stream);
 
-/* Test hooks for failure detection without a GPU fault.  key 1: the scan
- * tile with this index (value; -1 = off) never publishes its result, so its
- * successors' bounded waits run out.  key 2: the bounded wait's limit in
- * microseconds (default 2,000,000). */
+/* Test hooks for failure detection without a GPU fault.  key 1: the
+ * look-back tile with this index (value; -1 = off) never publishes its
+ * result, so its successors' bounded waits run out (the look-back scan
+ * variants and the re-reading batched variant).  key 2: the bounded wait's
+ * limit in microseconds (default 2,000,000). */
 int skel_set_debug(int key, int64_t value);
 
 /* ------------------------------------------------ measurement probes --- */

@@ -1176,7 +1176,8 @@ template <bool SCAN, bool RED, bool INCL, int R, int NC>
 __global__ void __launch_bounds__((kBrAggW + NC) * 32, 1)
 batched_br(const float *__restrict__ values, const int64_t *__restrict__ off, int64_t B, int64_t total,
            float *__restrict__ results, float *__restrict__ scan_out, const int *__restrict__ ok,
-           const BrMeta *__restrict__ meta, dev::LookbackDesc d, Control *ctl, uint32_t epoch, uint64_t limit_ns)
+           const BrMeta *__restrict__ meta, dev::LookbackDesc d, Control *ctl, uint32_t epoch, int64_t skip_tile,
+           uint64_t limit_ns)
 {
     constexpr int TE = kBrTE, NA = kBrAggW, QC = kBrQueue, CAP = kBrOffCap;
     constexpr uint32_t TB = TE * 4;
@@ -1322,7 +1323,9 @@ batched_br(const float *__restrict__ values, const int64_t *__restrict__ off, in
                     q += a_q[j];
                 }
                 const Pair tp((double)s, (double)q);
-                if (head) dev::Codec<Pair>::put(d.incl + t * 2, tp, epoch);   // depends on no earlier tile
+                if (t == skip_tile) {
+                    // test hook: this tile never publishes
+                } else if (head) dev::Codec<Pair>::put(d.incl + t * 2, tp, epoch);   // depends on no earlier tile
                 else dev::Codec<Pair>::put(d.agg + t * 2, tp, epoch);
                 const uint64_t w0 = dev::globaltimer();
                 for (uint32_t k = 0; k < (1u << 26); ++k) {   // room in the queue (bounded)
@@ -1423,7 +1426,7 @@ batched_br(const float *__restrict__ values, const int64_t *__restrict__ off, in
         // the prefix of the running instance: a look-back when it began in an earlier tile
         Pair p(0.0);
         if (!start_head) p = dev::lookback<Pair>(t, 0, Pair((double)agg.s, (double)agg.q), d, epoch, ctl, limit_ns, false);
-        if (lane == 0 && !start_head && !agg.h)   // no instance starts here: its prefix runs on
+        if (lane == 0 && !start_head && !agg.h && t != skip_tile)   // no instance starts here: its prefix runs on
             dev::Codec<Pair>::put(d.incl + t * 2, p + Pair((double)agg.s, (double)agg.q), epoch);
         const bool landed = __all_sync(0xffffffffu, wait_phase(&buf_full[cw], cpar));
         cpar ^= 1u;
@@ -1620,7 +1623,7 @@ int run_br_k(const BatchedLaunch &b, Control *ctl, uint64_t *words, const int *o
     dev::LookbackDesc d{words, words + 2 * ntiles};
     const DebugKnobs k = debug_knobs();
     launch_kernel(kern, (unsigned)(device_info().sms * occ), threads, (size_t)dyn, s, b.values, b.offsets, b.B,
-                  b.total, b.results, b.scan_out, ok, meta, d, ctl, epoch, k.wait_limit_ns);
+                  b.total, b.results, b.scan_out, ok, meta, d, ctl, epoch, k.scan_skip_publish_tile, k.wait_limit_ns);
     const cudaError_t e = cudaPeekAtLastError();
     return e == cudaSuccess ? SKEL_OK : fail_cuda(cudaGetLastError(), "batched reread launch");
 }
