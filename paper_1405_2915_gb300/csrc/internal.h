@@ -210,6 +210,7 @@ struct ScanLaunch {
     int64_t seg;    // segment length for row-wise scans (0: one segment)
 };
 int launch_scan(const ScanLaunch &sc, const Choice &c, cudaStream_t s);
+int scan_rr_launch(const ScanLaunch &sc, const Choice &c, cudaStream_t s);   // variant 8 (k_scan_rr.cu)
 int scan_variant_count();
 const char *scan_variant_name(int v);
 Choice scan_default();
@@ -294,6 +295,13 @@ struct BatchedLaunch {
 // count; the plan allocates them itself, the direct call uses the stream's
 // scratch).
 size_t batched_data_bytes(const BatchedLaunch &b, const Choice &c);
+// The flat segmented batched variants: 6 (k_batched_seg.cu; elements per
+// tile of a tile shape, and the call's launches) and 7 (k_batched_rr.cu).
+int batched_seg_tile(int tile);
+int batched_seg_launch(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, unsigned char *data,
+                       uint32_t epoch, cudaStream_t s);
+int batched_rr_launch(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words, unsigned char *data,
+                      uint32_t epoch, cudaStream_t s);
 size_t batched_word_count(const BatchedLaunch &b, const Choice &c);
 int launch_batched(const BatchedLaunch &b, const Choice &c, Control *ctl, uint64_t *words,
                    unsigned char *data, uint32_t epoch, cudaStream_t s);

@@ -129,7 +129,7 @@ def candidates(sk_name: str):
         yield (3, 256, 4, 0)
         yield (5, 256, 4, 0)
         yield (5, 256, 8, 0)
-        for t in range(4):       # the instances as one flat segmented scan, four tile shapes
+        for t in (0, 1):         # the instances as one flat segmented scan, two tile shapes
             yield (6, 256, 4, t)
         for t in (0, 1):         # flat, aggregators and re-reading scanners: ring tiles + scanners 6 + 6, 4 + 8
             yield (7, 256, 4, t)
