@@ -14,8 +14,10 @@ namespace {
 // 16-byte aligned, unlike per-instance frames, so short instances share a
 // tile instead of each taking one), staged partly in shared memory and
 // partly in registers as in scan variant 7, drawn in ticket order:
-//   heads:  the instance starts inside the tile (a binary search of the
-//           offsets), as a bitmap in shared memory;
+//   heads:  the instance starts inside the tile (from the instance holding
+//           the tile's first element, which the offsets check tabulates, on
+//           through the sorted offsets), as a bitmap in shared memory, with
+//           the first kSegOffCap of them listed for the result index;
 //   pass 1: each warp's (sum, sum of squares) since the last head of its
 //           range, and whether the range holds a head; one warp combines
 //           them in tile order, which gives every warp its carry and the
@@ -28,9 +30,10 @@ namespace {
 //           heads publishes its own);
 //   pass 2: each warp scans its elements (restarting at heads), stores them,
 //           and the last element of each instance writes its sum of squares.
-// The combine of (sum, sum of squares, has-head) triples in order is
-// (a, b) -> b.head ? b : (a.s + b.s, a.q + b.q, a.head).
-// Offsets of a tile's instances kept in shared memory by the flat variant.
+// Warp ranges with no instance start or end take a plain scan.  The combine
+// of (sum, sum of squares, has-head) triples is in batched_flat.cuh.
+
+// Offsets of a tile's instances kept in shared memory.
 constexpr int kSegOffCap = 512;
 
 // Offsets check for the flat variant: offsets[0] = 0, offsets[B] = total,
