@@ -670,8 +670,7 @@ def chains_leg(sk, torch, stream, steps: int = 10, reps: int = 3):
 # per-kernel algorithmic bytes per grid point of the composed loss's calls
 AUTOGRAD_BYTES = {"fwd_map_tanh": 8, "fwd_mapoverlap_9pt": 8, "fwd_sumsq_stencil": 4, "fwd_row_scan": 8,
                   "fwd_sumsq_scan": 4, "fwd_combine": 0, "bwd_scale": 0, "bwd_sumsq_stencil": 8,
-                  "bwd_mapoverlap_9pt": 8, "bwd_sumsq_scan": 8, "bwd_reverse_scan": 8, "bwd_add": 12,
-                  "bwd_map_tanh": 12}
+                  "bwd_mapoverlap_9pt": 8, "bwd_sumsq_scan": 8, "bwd_reverse_scan": 8, "bwd_map_tanh_sum": 16}
 
 
 def autograd_per_kernel(torch, stream, xg, reps: int = 5):

@@ -399,6 +399,13 @@ int skel_plan_destroy(skel_plan plan);
 int skel_map_bwd(skel_fn fn, const double *params, int nparams, const skel_handle *ins, int nin,
                  skel_handle gout, skel_handle *gins, void *stream);
 
+/* skel_map_bwd when the map's output feeds several calls (a composition of
+ * calls, Sec. II): the upstream gradient is gouts[0] + gouts[1] (ngout 1 or
+ * 2, same length and type), added inside the adjoint's own pass instead of
+ * by a separate Map (ADD) call.  Otherwise as skel_map_bwd. */
+int skel_map_bwd_sum(skel_fn fn, const double *params, int nparams, const skel_handle *ins, int nin,
+                     const skel_handle *gouts, int ngout, skel_handle *gins, void *stream);
+
 /* Adjoint of skel_reduce with ADD: gin[i] = gr for every i (a broadcast);
  * gr is a 1-element F32 container (device) or, if gr is NULL, *gr_host. */
 int skel_reduce_bwd(skel_fn op, skel_handle gr, const float *gr_host, skel_handle gin,

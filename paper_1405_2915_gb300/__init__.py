@@ -352,6 +352,13 @@ def skel_map_bwd(fn, ins: Sequence[Container], gout: Container, gins: Sequence[C
     check(lib.skel_map_bwd(_fn(fn), p, n, _handles(ins), len(ins), gout.handle, _handles(gins), _stream(stream)))
 
 
+def skel_map_bwd_sum(fn, ins: Sequence[Container], gouts: Sequence[Container], gins: Sequence[Container | None],
+                     params=(), stream=None) -> None:
+    p, n = _params(params)
+    check(lib.skel_map_bwd_sum(_fn(fn), p, n, _handles(ins), len(ins), _handles(gouts), len(gouts), _handles(gins),
+                               _stream(stream)))
+
+
 def skel_reduce_bwd(op, gr: Container | None, gin: Container, gr_host: float | None = None, stream=None) -> None:
     g = None if gr_host is None else C.byref(C.c_float(gr_host))
     check(lib.skel_reduce_bwd(_fn(op), None if gr is None else gr.handle, g, gin.handle, _stream(stream)))

@@ -61,6 +61,7 @@ SIGNATURES = {
     "skel_plan_launch": (i32, [vp, vp]),
     "skel_plan_destroy": (i32, [vp]),
     "skel_map_bwd": (i32, [i32, C.POINTER(dbl), i32, C.POINTER(vp), i32, vp, C.POINTER(vp), vp]),
+    "skel_map_bwd_sum": (i32, [i32, C.POINTER(dbl), i32, C.POINTER(vp), i32, C.POINTER(vp), i32, C.POINTER(vp), vp]),
     "skel_reduce_bwd": (i32, [i32, vp, f32p, vp, vp]),
     "skel_mapreduce_bwd": (i32, [i32, i32, C.POINTER(vp), i32, vp, f32p, C.POINTER(vp), vp]),
     "skel_scan_bwd": (i32, [i32, i32, vp, vp, vp]),

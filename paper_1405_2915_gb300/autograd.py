@@ -9,8 +9,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (Container, skel_map, skel_map_bwd, skel_mapoverlap, skel_mapoverlap_bwd, skel_mapreduce,
-               skel_mapreduce_bwd, skel_reduce, skel_reduce_bwd, skel_scan, skel_scan_bwd)
+from . import (Container, skel_map, skel_map_bwd, skel_map_bwd_sum, skel_mapoverlap, skel_mapoverlap_bwd,
+               skel_mapreduce, skel_mapreduce_bwd, skel_reduce, skel_reduce_bwd, skel_scan, skel_scan_bwd)
 
 
 def _c(t: torch.Tensor) -> Container:
@@ -141,7 +141,8 @@ def _call(step, name: str, fn) -> None:
 class ComposedLossFn(torch.autograd.Function):
     """The differentiable composed pipeline as one Function, so that the
     gradients of its two branches (t feeds both the stencil and the row scan)
-    are added by a skeleton call instead of by torch's autograd engine.
+    are added by a skeleton call instead of by torch's autograd engine (the
+    tanh adjoint takes both and adds them in its own pass).
 
     Forward (skeleton calls):
         t = tanh(x)                              Map
@@ -151,8 +152,9 @@ class ComposedLossFn(torch.autograd.Function):
     Backward, with g = dL (a device scalar):
         gc = g / (rows * cols)                   Map (scale on the scalar)
         gt = S^T (2 u g)                         MapReduce adjoint, transposed stencil
-        gt += rscan(2 s gc)                      MapReduce adjoint, reverse scan, Map (add, in place)
-        gx = gt (1 - t^2)                        Map adjoint of tanh (from the saved t)
+        gt2 = rscan(2 s gc)                      MapReduce adjoint, reverse scan
+        gx = (gt + gt2) (1 - t^2)                Map adjoint of tanh (from the saved t) over the
+                                                 sum of the two branches' gradients, one pass
     `step(name, thunk)`, when given, runs each call (the benchmark times
     them one by one); the calls and their order are the same either way."""
 
@@ -187,8 +189,7 @@ class ComposedLossFn(torch.autograd.Function):
         _call(step, "bwd_mapoverlap_9pt", lambda: skel_mapoverlap_bwd("stencil9", 1, weights, boundary, _c(gu), cgt))
         _call(step, "bwd_sumsq_scan", lambda: skel_mapreduce_bwd("sq", "add", [_c(s)], cgc, [_c(gs)]))
         _call(step, "bwd_reverse_scan", lambda: skel_scan_bwd("add", True, _c(gs), _c(gt2)))
-        _call(step, "bwd_add", lambda: skel_map("add", [cgt, _c(gt2)], cgt))
-        _call(step, "bwd_map_tanh", lambda: skel_map_bwd("tanh", [_c(t)], cgt, [_c(gx)], [1.0]))
+        _call(step, "bwd_map_tanh_sum", lambda: skel_map_bwd_sum("tanh", [_c(t)], [cgt, _c(gt2)], [_c(gx)], [1.0]))
         return gx, None, None, None
 
 

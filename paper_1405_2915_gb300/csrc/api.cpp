@@ -1343,13 +1343,23 @@ int skel_plan_destroy(skel_plan plan)
 int skel_map_bwd(skel_fn fn, const double *params, int nparams, const skel_handle *ins, int nin, skel_handle gout,
                  skel_handle *gins, void *stream)
 {
+    return skel_map_bwd_sum(fn, params, nparams, ins, nin, &gout, 1, gins, stream);
+}
+
+int skel_map_bwd_sum(skel_fn fn, const double *params, int nparams, const skel_handle *ins, int nin,
+                     const skel_handle *gouts, int ngout, skel_handle *gins, void *stream)
+{
     return guarded([&] {
+        if (!gouts || ngout < 1 || ngout > 2) return fail(SKEL_ERR_INVALID_ARG, "map_bwd: one or two upstream gradients");
+        const skel_handle gout = gouts[0];
         const int need = map_nin(fn);
         if (!need) return fail(SKEL_ERR_UNSUPPORTED, "map_bwd: function not offered");
         if (fn == SKEL_FN_MAX) return fail(SKEL_ERR_UNSUPPORTED, "map_bwd: MAX has no adjoint here");
         if (nin != need || !ins || !gins) return fail(SKEL_ERR_INVALID_ARG, "map_bwd: wrong number of inputs");
         if (map_needs_param(fn) && (!params || nparams < 1)) return fail(SKEL_ERR_INVALID_ARG, "map_bwd: needs params[0]");
         if (!valid_handle(gout) || gout->dtype != SKEL_F32) return fail(SKEL_ERR_INVALID_ARG, "bad gout");
+        if (ngout == 2 && (!valid_handle(gouts[1]) || gouts[1]->dtype != SKEL_F32 || gouts[1]->n != gout->n))
+            return fail(SKEL_ERR_SHAPE, "map_bwd: the second upstream gradient must match the first");
         const bool from_out = fn == SKEL_FN_TANH && params && nparams >= 1 && params[0] == 1.0;
         std::vector<Operand> ops;
         for (int k = 0; k < nin; ++k) {
@@ -1358,6 +1368,7 @@ int skel_map_bwd(skel_fn fn, const double *params, int nparams, const skel_handl
             ops.push_back({ins[k], SKEL_READ});
         }
         ops.push_back({gout, SKEL_READ});
+        if (ngout == 2) ops.push_back({gouts[1], SKEL_READ});
         int outs = 0;
         for (int k = 0; k < nin; ++k) {
             if (!gins[k]) continue;
@@ -1377,7 +1388,8 @@ int skel_map_bwd(skel_fn fn, const double *params, int nparams, const skel_handl
         m.in0 = (const float *)ops[0].ptr;
         m.in1 = nin == 2 ? (const float *)ops[1].ptr : nullptr;
         m.g = (const float *)ops[nin].ptr;
-        size_t k = nin + 1;
+        m.g2 = ngout == 2 ? (const float *)ops[nin + 1].ptr : nullptr;
+        size_t k = nin + ngout;
         m.gin0 = gins[0] ? (float *)ops[k++].ptr : nullptr;
         m.gin1 = (nin == 2 && gins[1]) ? (float *)ops[k++].ptr : nullptr;
         m.n = gout->n;

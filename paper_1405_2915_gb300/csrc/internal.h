@@ -317,6 +317,7 @@ struct MapBwdLaunch {
     const float *in0;
     const float *in1;
     const float *g;      // per-element upstream gradient (NULL: use *g_scalar)
+    const float *g2;     // a second per-element upstream gradient added to g, or NULL
     const float *g_scalar_dev;  // device scalar (mapreduce/reduce adjoint), or NULL
     float g_scalar_host;
     float *gin0;

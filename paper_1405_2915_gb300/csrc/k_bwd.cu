@@ -2,8 +2,9 @@
 // of MapReduce (the upstream scalar times the map's derivative) and of
 // Reduce with (+) (a broadcast of the upstream scalar).
 //   gin0[i] = g_i * df/dx(x_i, y_i),  gin1[i] = g_i * df/dy(x_i, y_i)
-// where g_i is the per-element upstream gradient or one upstream scalar (a
-// device word or a host value).  16-byte accesses when every operand is
+// where g_i is the per-element upstream gradient (or the sum of two, when
+// the map's output fed two calls) or one upstream scalar (a device word or a
+// host value).  16-byte accesses when every operand is
 // 16-byte aligned, scalar otherwise.
 #include "common.cuh"
 
@@ -16,6 +17,7 @@ struct BwdArgs {
     const float *x;
     const float *y;
     const float *g;        // per element, or NULL
+    const float *g2;       // a second per-element gradient added to g, or NULL
     const float *gs_dev;   // scalar on the device, or NULL
     float gs_host;
     float *gx;
@@ -39,7 +41,8 @@ __device__ __forceinline__ void dfun(float x, float y, float a, int from_out, fl
 template <int FN>
 __device__ __forceinline__ void one(const BwdArgs &p, int64_t i, float gsc)
 {
-    const float g = p.g ? p.g[i] : gsc;
+    float g = p.g ? p.g[i] : gsc;
+    if (p.g2) g += p.g2[i];
     const float x = p.x ? p.x[i] : 0.f, y = p.y ? p.y[i] : 0.f;
     float dx, dy;
     dfun<FN>(x, y, p.a, p.tanh_from_output, dx, dy);
@@ -60,6 +63,13 @@ __global__ void __launch_bounds__(256) map_bwd_kernel(BwdArgs p)
     const int64_t nv = p.n / 4;
     for (int64_t v = t; v < nv; v += stride) {
         float4 g4 = p.g ? dev::ld_stream(reinterpret_cast<const float4 *>(p.g) + v) : make_float4(gsc, gsc, gsc, gsc);
+        if (p.g2) {
+            const float4 h4 = dev::ld_stream(reinterpret_cast<const float4 *>(p.g2) + v);
+            g4.x += h4.x;
+            g4.y += h4.y;
+            g4.z += h4.z;
+            g4.w += h4.w;
+        }
         float4 x4 = p.x ? dev::ld_stream(reinterpret_cast<const float4 *>(p.x) + v) : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 y4 = p.y ? dev::ld_stream(reinterpret_cast<const float4 *>(p.y) + v) : make_float4(0.f, 0.f, 0.f, 0.f);
         const float *gv = &g4.x, *xv = &x4.x, *yv = &y4.x;
@@ -81,7 +91,8 @@ __global__ void __launch_bounds__(256) map_bwd_kernel(BwdArgs p)
 template <int FN>
 int run(const BwdArgs &p, cudaStream_t s)
 {
-    const bool vec = aligned16(p.x) && aligned16(p.y) && aligned16(p.g) && aligned16(p.gx) && aligned16(p.gy);
+    const bool vec = aligned16(p.x) && aligned16(p.y) && aligned16(p.g) && aligned16(p.g2) && aligned16(p.gx) &&
+                     aligned16(p.gy);
     int64_t grid = ceil_div(vec ? ceil_div(p.n, 4) : p.n, 256);
     const int64_t cap = (int64_t)device_info().sms * 8 * 8;
     if (grid > cap) grid = cap;
@@ -97,7 +108,7 @@ int run(const BwdArgs &p, cudaStream_t s)
 int launch_map_bwd(const MapBwdLaunch &m, cudaStream_t s)
 {
     if (m.n == 0) return SKEL_OK;
-    BwdArgs p{m.a, m.tanh_from_output, m.in0, m.in1, m.g, m.g_scalar_dev, m.g_scalar_host, m.gin0, m.gin1, m.n};
+    BwdArgs p{m.a, m.tanh_from_output, m.in0, m.in1, m.g, m.g2, m.g_scalar_dev, m.g_scalar_host, m.gin0, m.gin1, m.n};
     switch (m.fn) {
     case SKEL_FN_AXPY: return run<SKEL_FN_AXPY>(p, s);
     case SKEL_FN_ADD: return run<SKEL_FN_ADD>(p, s);

@@ -31,6 +31,35 @@ def test_map_bwd(fn, n, pad):
         assert_elem_close(to_np(gy), ry, f"{fn} dy")
 
 
+@pytest.mark.parametrize("fn", ["axpy", "mul", "tanh", "sq"])
+@pytest.mark.parametrize("n,pad", [(5, 0), (100_003, 0), (100_003, 1)])
+def test_map_bwd_sum_of_two_upstream_gradients(fn, n, pad):
+    """The adjoint of a map whose output fed two calls: the two upstream
+    gradients are added (float32, one rounding, as a separate Map ADD would)
+    inside the adjoint's pass; compared with the oracle adjoint of that sum.
+    A second gradient of another length is refused."""
+    import torch
+    sk = skel()
+    two = fn in ("axpy", "mul")
+    x, y = syn.uniform_f32(11, n), syn.uniform_f32(12, n)
+    g1, g2 = syn.uniform_f32(13, n), syn.uniform_f32(14, n)
+    ins = [wrap(dev_tensor(x, pad))] + ([wrap(dev_tensor(y, pad))] if two else [])
+    gx = dev_empty((n,), torch.float32, pad)
+    gy = dev_empty((n,), torch.float32, pad) if two else None
+    params = [2.5] if fn == "axpy" else []
+    sk.skel_map_bwd_sum(fn, ins, [wrap(dev_tensor(g1, pad)), wrap(dev_tensor(g2, pad))],
+                        [wrap(gx)] + ([wrap(gy)] if two else []), params=params)
+    g = (g1 + g2).astype(np.float32)
+    rx, ry = oracle.map_bwd_f32(fn, g, x, y if two else None, a=2.5)
+    assert_elem_close(to_np(gx), rx, f"{fn} dx, summed upstream")
+    if two:
+        assert_elem_close(to_np(gy), ry, f"{fn} dy, summed upstream")
+    with pytest.raises(sk.SkelError) as e:
+        sk.skel_map_bwd_sum(fn, ins, [wrap(dev_tensor(g1)), wrap(dev_tensor(g2[:-1] if n > 1 else g2[:0]))],
+                            [wrap(gx)] + ([wrap(gy)] if two else []), params=params)
+    assert e.value.code == -2
+
+
 def test_tanh_bwd_from_saved_output():
     """gx = g (1 - t^2) from the saved t = tanhf(x) against g (1 - tanh(x)^2)
     in float64, within the elementwise 1e-6: tanhf is within 2 ulp, so
